@@ -1,0 +1,154 @@
+/*
+ * lcs.h — C ABI of the GB300 (sm_103a) LCS library (liblcs.so).
+ *
+ * The library fills the dynamic-programming table of the longest common subsequence (LCS) of two byte strings and
+ * traces one LCS back, as defined in Dash & Nayak, "Parallel Algorithm for Longest Common Subsequence in a String":
+ *
+ *   c[i,0] = c[0,j] = 0;  c[i,j] = c[i-1,j-1] + 1 if x_i = y_j, else max(c[i-1,j], c[i,j-1])   (§I.B, §I.C)
+ *
+ * X = x_1..x_m indexes the rows and Y = y_1..y_n the columns; the LCS length is c[m,n] (§I.C, LCS-length). The
+ * traced string is the one Print-LCS (§I.D) emits from b[m,n] when b takes the paper's tie-break: DIAG on every
+ * match, otherwise UP when c[i-1,j] >= c[i,j-1] and LEFT when not. Symbols are bytes (0..255) compared for
+ * equality; DNA over {A,C,G,T} (§I) is one case of that.
+ *
+ * Conventions for every call:
+ *   - Return value: LCS_OK (0) or a negative LCS_ERR_* code; lcs_serve_poll may also return LCS_PENDING. No C++
+ *     exception crosses this boundary.
+ *   - Sizes are element counts (bytes for strings). A pointer may be NULL only when its size is 0.
+ *   - Host pointers are ordinary (pageable or pinned) host memory. "_dev" calls take device pointers (for instance
+ *     the data_ptr() of CUDA tensors) and a cudaStream_t passed as void* (NULL = the context's own stream); they
+ *     return after enqueueing the work, which then runs in stream order.
+ *   - The caller owns every buffer it passes; the library never keeps a caller pointer past the call (serving
+ *     copies its inputs at submit).
+ *   - A context serialises its own calls with an internal lock; use one context per host thread for concurrency.
+ */
+#ifndef LCS_H_
+#define LCS_H_
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LCS_API __attribute__((visibility("default")))
+#else
+#define LCS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------------------------------- */
+#define LCS_OK 0
+#define LCS_PENDING 1          /* lcs_serve_poll: the request is admitted or queued but not finished yet */
+#define LCS_ERR_INVALID -1     /* bad argument: NULL with a nonzero size, m*n overflow, unknown ticket, ... */
+#define LCS_ERR_NOMEM -2       /* device memory for the request could not be allocated (or can never fit) */
+#define LCS_ERR_CAPACITY -3    /* output buffer too small; *out_len holds the required size */
+#define LCS_ERR_BUSY -4        /* serving queue full (back-pressure); retry later */
+#define LCS_ERR_TIMEOUT -5     /* a bounded device-side wait expired (the kernel returned instead of hanging) */
+#define LCS_ERR_CUDA -6        /* a CUDA runtime call failed */
+#define LCS_ERR_INTERNAL -7    /* an internal consistency check failed */
+
+/* Human-readable text for a status code (static storage; never NULL). */
+LCS_API const char* lcs_strerror(int status);
+
+/* ---- context ------------------------------------------------------------------------------------------------ */
+typedef struct lcs_ctx lcs_ctx;
+
+/* Creates a context on CUDA device `device`: its own non-blocking streams, grow-only device scratch buffers and
+ * pinned staging buffers. *out receives the handle. Errors: LCS_ERR_INVALID (out NULL or no such device),
+ * LCS_ERR_CUDA. */
+LCS_API int lcs_ctx_create(int device, lcs_ctx** out);
+
+/* Waits for all work of the context and frees everything it owns. NULL is ignored. */
+LCS_API void lcs_ctx_destroy(lcs_ctx* ctx);
+
+/* Waits for the context's streams and returns (and clears) any error latched by an earlier "_dev" call's kernels
+ * (LCS_ERR_TIMEOUT, LCS_ERR_INTERNAL) or LCS_OK. */
+LCS_API int lcs_ctx_sync(lcs_ctx* ctx);
+
+/* ---- length (paper §I.C, LCS-length; returns c[m,n]) --------------------------------------------------------- */
+
+/* Host buffers x[0..m), y[0..n); writes c[m,n] to *out_len. Blocking. m = 0 or n = 0 gives 0. Errors:
+ * LCS_ERR_INVALID (NULL with nonzero size, out_len NULL), LCS_ERR_NOMEM, LCS_ERR_CUDA, LCS_ERR_TIMEOUT. */
+LCS_API int lcs_length(lcs_ctx* ctx, const uint8_t* x, uint64_t m, const uint8_t* y, uint64_t n, uint64_t* out_len);
+
+/* Device buffers; writes c[m,n] to the device word *d_out_len in stream order. Asynchronous; kernel-side errors
+ * are latched and reported by lcs_ctx_sync. */
+LCS_API int lcs_length_dev(lcs_ctx* ctx, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, uint64_t n,
+                   uint64_t* d_out_len, void* stream);
+
+/* ---- traceback (paper §I.C LCS-length with table b, then §I.D Print-LCS) -------------------------------------- */
+
+/* Host buffers. Writes the LCS (forward order) to out[0..len) and len to *out_len. out_cap >= min(m, n) is always
+ * enough; a smaller out_cap that cannot hold the result gives LCS_ERR_CAPACITY with *out_len = the LCS length.
+ * Device memory of about m*n/8 bytes (a 1-bit-per-cell direction bitmap) is needed: LCS_ERR_NOMEM when it
+ * cannot be allocated. Blocking. */
+LCS_API int lcs_traceback(lcs_ctx* ctx, const uint8_t* x, uint64_t m, const uint8_t* y, uint64_t n, uint8_t* out,
+                  uint64_t out_cap, uint64_t* out_len);
+
+/* Device buffers: d_out (capacity out_cap >= min(m, n), else LCS_ERR_CAPACITY at the call) receives the LCS and
+ * the device word *d_out_len its length. Asynchronous in `stream`. */
+LCS_API int lcs_traceback_dev(lcs_ctx* ctx, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, uint64_t n,
+                      uint8_t* d_out, uint64_t out_cap, uint64_t* d_out_len, void* stream);
+
+/* ---- batch: many independent pairs, lengths only (c[m_k, n_k] for every pair k) ------------------------------- */
+
+/* Pair k is x = xs[x_off[k] .. x_off[k+1]) and y = ys[y_off[k] .. y_off[k+1]) (count+1 offsets each, non-
+ * decreasing, host memory). out_lens[k] receives its LCS length. Blocking. Errors: LCS_ERR_INVALID (bad offsets),
+ * LCS_ERR_NOMEM, LCS_ERR_CUDA, LCS_ERR_TIMEOUT. */
+LCS_API int lcs_batch(lcs_ctx* ctx, const uint8_t* xs, const uint64_t* x_off, const uint8_t* ys, const uint64_t* y_off,
+              uint64_t count, uint64_t* out_lens);
+
+/* The same with device buffers (offsets too); asynchronous in `stream`. */
+LCS_API int lcs_batch_dev(lcs_ctx* ctx, const uint8_t* d_xs, const uint64_t* d_x_off, const uint8_t* d_ys,
+                  const uint64_t* d_y_off, uint64_t count, uint64_t* d_out_lens, void* stream);
+
+/* ---- serving: continuous batching of requests that arrive over time ------------------------------------------- */
+typedef struct lcs_server lcs_server;
+
+#define LCS_TRACEBACK 1u /* submit flag: also return the LCS string (else length only) */
+
+typedef struct lcs_serve_cfg {
+  uint32_t max_queue;          /* requests waiting or in flight before submit returns LCS_ERR_BUSY (0 = 65536) */
+  uint32_t max_batch;          /* short pairs packed into one batched launch (0 = 4096) */
+  uint64_t hbm_budget_bytes;   /* device bytes the server may hold for traceback bitmaps (0 = 60% of free) */
+  uint32_t long_pair_cells_log2; /* pairs with m*n >= 2^this run on the single-pair path (0 = 2^24) */
+  uint32_t reserved;
+} lcs_serve_cfg;
+
+typedef struct lcs_result {
+  int32_t status;              /* LCS_OK or the request's error code */
+  uint32_t flags;              /* the submit flags */
+  uint64_t length;             /* c[m,n] */
+  const uint8_t* lcs;          /* traceback string (server-owned until lcs_result_release), NULL if none */
+  uint64_t lcs_len;            /* bytes at lcs */
+  double submit_to_done_s;     /* latency measured by the server: submit() to result ready */
+} lcs_result;
+
+/* Creates a server on ctx (the server then owns the context's streams until lcs_serve_destroy; do not call other
+ * functions on ctx meanwhile). cfg may be NULL for defaults. */
+LCS_API int lcs_serve_create(lcs_ctx* ctx, const lcs_serve_cfg* cfg, lcs_server** out);
+
+/* Copies x and y and queues the request; *ticket identifies it. Errors: LCS_ERR_BUSY (queue full),
+ * LCS_ERR_NOMEM (a traceback whose bitmap can never fit the budget), LCS_ERR_INVALID. */
+LCS_API int lcs_serve_submit(lcs_server* srv, const uint8_t* x, uint64_t m, const uint8_t* y, uint64_t n, uint32_t flags,
+                     uint64_t* ticket);
+
+/* Non-blocking: LCS_OK and *out filled when the request is done, LCS_PENDING while it is not, LCS_ERR_INVALID for
+ * an unknown or released ticket. */
+LCS_API int lcs_serve_poll(lcs_server* srv, uint64_t ticket, lcs_result* out);
+
+/* Blocking variant of lcs_serve_poll with a timeout in seconds (< 0 waits forever); LCS_PENDING on timeout. */
+LCS_API int lcs_serve_wait(lcs_server* srv, uint64_t ticket, double timeout_s, lcs_result* out);
+
+/* Frees a finished request's result (its lcs string pointer becomes invalid). */
+LCS_API void lcs_result_release(lcs_server* srv, uint64_t ticket);
+
+/* Finishes in-flight work, frees all results and stops the scheduler thread. NULL is ignored. */
+LCS_API void lcs_serve_destroy(lcs_server* srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LCS_H_ */

@@ -1,0 +1,398 @@
+// C ABI of liblcs.so: contexts, LCS length and traceback for one pair (paper §I.C LCS-length, §I.D Print-LCS).
+// Host code only; the kernels live in lcs_prep.cu, lcs_fill.cu and lcs_trace.cu.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "lcs_ctx.h"
+
+using namespace lcs;
+
+extern "C" const char* lcs_strerror(int status) {
+  switch (status) {
+    case LCS_OK: return "ok";
+    case LCS_PENDING: return "pending";
+    case LCS_ERR_INVALID: return "invalid argument";
+    case LCS_ERR_NOMEM: return "out of device memory";
+    case LCS_ERR_CAPACITY: return "output buffer too small";
+    case LCS_ERR_BUSY: return "queue full";
+    case LCS_ERR_TIMEOUT: return "device wait timed out";
+    case LCS_ERR_CUDA: return "CUDA error";
+    case LCS_ERR_INTERNAL: return "internal consistency check failed";
+    default: return "unknown status";
+  }
+}
+
+namespace lcs {
+
+int from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return LCS_OK;
+  cudaGetLastError();  // clear a sticky-free error so the context stays usable
+  if (e == cudaErrorMemoryAllocation) return LCS_ERR_NOMEM;
+  return LCS_ERR_CUDA;
+}
+
+cudaError_t ensure(DBuf& b, size_t bytes) {
+  if (bytes <= b.cap) return cudaSuccess;
+  if (b.p) {
+    cudaError_t e = cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    if (e != cudaSuccess) return e;
+  }
+  const size_t want = std::max<size_t>(bytes + bytes / 8, 256);
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e;
+  }
+  b.p = p;
+  b.cap = want;
+  return cudaSuccess;
+}
+
+void release(DBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+}
+
+// Latched device status: returns its error (if any) and clears it. Caller has synchronised the stream.
+int take_status(lcs_ctx* c) {
+  DevStatus h{};
+  if (cudaMemcpy(&h, c->status(), sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return from_cuda(cudaGetLastError());
+  if (h.flags == 0) return LCS_OK;
+  cudaMemset(c->status(), 0, sizeof(DevStatus));
+  if (h.flags & kStatTimeout) return LCS_ERR_TIMEOUT;
+  return LCS_ERR_INTERNAL;
+}
+
+// Runs one or two fill jobs: one cooperative launch when all their blocks fit on the GPU at once, otherwise each
+// job alone, in passes of at most max_coop blocks (the carry slots between passes are complete in memory).
+int run_fill(lcs_ctx* c, FillJob* jobs, int njobs, bool traceback, cudaStream_t st) {
+  FillArgs a{};
+  a.status = c->status();
+  a.spin_limit = c->spin_limit;
+  uint32_t total = 0;
+  for (int k = 0; k < njobs; ++k) total += jobs[k].nblocks_total;
+  if (total <= (uint32_t)c->max_coop) {
+    for (int k = 0; k < njobs; ++k) {
+      a.job[k] = jobs[k];
+      a.job[k].block0 = 0;
+      a.job[k].nblocks = jobs[k].nblocks_total;
+    }
+    a.njobs = (uint32_t)njobs;
+    return from_cuda(launch_fill(a, 8, traceback, st));
+  }
+  for (int k = 0; k < njobs; ++k) {
+    for (uint32_t b0 = 0; b0 < jobs[k].nblocks_total; b0 += (uint32_t)c->max_coop) {
+      a.job[0] = jobs[k];
+      a.job[0].block0 = b0;
+      a.job[0].nblocks = std::min<uint32_t>((uint32_t)c->max_coop, jobs[k].nblocks_total - b0);
+      a.njobs = 1;
+      int rc = from_cuda(launch_fill(a, 8, traceback, st));
+      if (rc) return rc;
+    }
+  }
+  return LCS_OK;
+}
+
+// Geometry of one table: words per row (one extra word catches the carry out of column n), blocks, lanes.
+struct Geo {
+  uint64_t wq, nblocks, wpad;
+};
+static Geo geo_for(uint64_t n) {
+  Geo g;
+  g.wq = n / 32 + 1;
+  g.nblocks = (g.wq + kStripeWords - 1) / kStripeWords;
+  g.wpad = g.nblocks * kStripeWords;
+  return g;
+}
+
+// Prepares the alphabet, the match masks of Y (forward and, if wanted, reversed) into the context buffers.
+static int prep_y(lcs_ctx* c, const uint8_t* d_y, uint64_t n, const Geo& g, bool want_rev, cudaStream_t st) {
+  int rc = from_cuda(ensure(c->peq_f, (size_t)kSigmaMax * g.wpad * 4));
+  if (!rc && want_rev) rc = from_cuda(ensure(c->peq_r, (size_t)kSigmaMax * g.wpad * 4));
+  if (rc) return rc;
+  rc = from_cuda(launch_alphabet(d_y, n, c->presence(), c->codemap(), c->sigma(), st));
+  if (!rc) rc = from_cuda(launch_peq(d_y, n, false, g.wpad, c->codemap(), (uint32_t*)c->peq_f.p, st));
+  if (!rc && want_rev) rc = from_cuda(launch_peq(d_y, n, true, g.wpad, c->codemap(), (uint32_t*)c->peq_r.p, st));
+  return rc;
+}
+
+int run_length(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, uint64_t n, uint64_t* d_out,
+               cudaStream_t st) {
+  if (m == 0 || n == 0) return from_cuda(cudaMemsetAsync(d_out, 0, sizeof(uint64_t), st));
+  const uint32_t B = 8;
+  const Geo g = geo_for(n);
+  // Meet in the middle: the top half of the rows forward, the bottom half on the reversed strings, at the same
+  // time; L = max_j (c[mt, j] + LCS(X[mt+1..m], Y[j+1..n])) (the recurrence read from both ends).
+  const bool split = m >= 2 * B && 2 * g.nblocks <= (uint64_t)c->max_coop;
+  const uint64_t mt = split ? B * (m / (2 * B)) : m;
+  const uint64_t mb = m - mt;
+  const uint64_t Rf = (mt + B - 1) / B;
+  const uint64_t padr = split ? (B - mb % B) % B : 0;
+  const uint64_t Rr = split ? (mb + padr) / B : 0;
+  int rc = prep_y(c, d_y, n, g, split, st);
+  if (rc) return rc;
+  rc = from_cuda(ensure(c->xoff_f, (Rf + 2 * kPadRowblocks) * B * 4));
+  if (!rc) rc = from_cuda(ensure(c->carry_f, g.nblocks * Rf * 4));
+  if (!rc) rc = from_cuda(ensure(c->fv_f, g.wpad * 4));
+  if (!rc && split) rc = from_cuda(ensure(c->xoff_r, (Rr + 2 * kPadRowblocks) * B * 4));
+  if (!rc && split) rc = from_cuda(ensure(c->carry_r, g.nblocks * Rr * 4));
+  if (!rc && split) rc = from_cuda(ensure(c->fv_r, g.wpad * 4));
+  if (!rc && split) rc = from_cuda(ensure(c->colsum, (2 * (g.wq + 1) + 4) * 4));
+  if (rc) return rc;
+  rc = from_cuda(launch_xoff(d_x, mt, false, 0, Rf, B, c->codemap(), c->sigma(), (uint32_t*)c->xoff_f.p, nullptr, st));
+  if (!rc && split)
+    rc = from_cuda(launch_xoff(d_x + mt, mb, true, padr, Rr, B, c->codemap(), c->sigma(), (uint32_t*)c->xoff_r.p,
+                               nullptr, st));
+  if (!rc) rc = from_cuda(cudaMemsetAsync(c->carry_f.p, 0, g.nblocks * Rf * 4, st));
+  if (!rc && split) rc = from_cuda(cudaMemsetAsync(c->carry_r.p, 0, g.nblocks * Rr * 4, st));
+  if (!rc) rc = from_cuda(cudaMemsetAsync(c->len_acc(), 0, sizeof(unsigned long long), st));
+  if (rc) return rc;
+  FillJob jobs[2]{};
+  jobs[0].xoff = (const uint32_t*)c->xoff_f.p;
+  jobs[0].peq = (const uint32_t*)c->peq_f.p;
+  jobs[0].sigma_rows = c->sigma();
+  jobs[0].carry = (uint32_t*)c->carry_f.p;
+  jobs[0].final_v = split ? (uint32_t*)c->fv_f.p : nullptr;
+  jobs[0].len_acc = split ? nullptr : c->len_acc();
+  jobs[0].R = Rf;
+  jobs[0].wpad = g.wpad;
+  jobs[0].nblocks_total = (uint32_t)g.nblocks;
+  if (split) {
+    jobs[1] = jobs[0];
+    jobs[1].xoff = (const uint32_t*)c->xoff_r.p;
+    jobs[1].peq = (const uint32_t*)c->peq_r.p;
+    jobs[1].carry = (uint32_t*)c->carry_r.p;
+    jobs[1].final_v = (uint32_t*)c->fv_r.p;
+    jobs[1].len_acc = nullptr;
+    jobs[1].R = Rr;
+  }
+  rc = run_fill(c, jobs, split ? 2 : 1, false, st);
+  if (rc) return rc;
+  if (split)
+    return from_cuda(launch_combine((const uint32_t*)c->fv_f.p, (const uint32_t*)c->fv_r.p, n, g.wq,
+                                    (uint32_t*)c->colsum.p, (unsigned long long*)d_out, st));
+  return from_cuda(cudaMemcpyAsync(d_out, c->len_acc(), sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
+}
+
+int run_traceback(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, uint64_t n, uint8_t* d_out,
+                  uint64_t out_cap, uint64_t* d_out_len, cudaStream_t st) {
+  if (m == 0 || n == 0) return from_cuda(cudaMemsetAsync(d_out_len, 0, sizeof(uint64_t), st));
+  const uint32_t B = 8;
+  const Geo g = geo_for(n);
+  // Segments of H rows (a multiple of B) for the parallel walk; at most kMaxSegments of them.
+  uint64_t H = (m + kMaxSegments - 1) / kMaxSegments;
+  H = std::max<uint64_t>(B, (H + B - 1) / B * B);
+  const uint64_t S = (m + H - 1) / H;
+  const bool rev = S > 1;
+  const uint64_t Rf = (m + B - 1) / B;
+  const uint64_t padr = S * H - m;
+  const uint64_t Rr = rev ? (S * H) / B : 0;
+  const uint64_t nwarps = g.nblocks * kFillWarps;
+  const size_t t_bytes = (size_t)nwarps * (Rf + 31) * 32 * B * 4;
+  int rc = prep_y(c, d_y, n, g, rev, st);
+  if (rc) return rc;
+  rc = from_cuda(ensure(c->T, t_bytes));
+  if (!rc) rc = from_cuda(ensure(c->xoff_f, (Rf + 2 * kPadRowblocks) * B * 4));
+  if (!rc) rc = from_cuda(ensure(c->xcode, m));
+  if (!rc) rc = from_cuda(ensure(c->carry_f, g.nblocks * Rf * 4));
+  if (!rc) rc = from_cuda(ensure(c->snap_f, S * g.wpad * 4));
+  if (!rc && rev) rc = from_cuda(ensure(c->xoff_r, (Rr + 2 * kPadRowblocks) * B * 4));
+  if (!rc && rev) rc = from_cuda(ensure(c->carry_r, g.nblocks * Rr * 4));
+  if (!rc && rev) rc = from_cuda(ensure(c->snap_r, S * g.wpad * 4));
+  if (!rc) rc = from_cuda(ensure(c->colsum, (S * 2 * (g.wq + 1) + 4) * 4));
+  if (!rc) rc = from_cuda(ensure(c->ent, S * kWalkers * 4));
+  if (!rc) rc = from_cuda(ensure(c->ext, S * kWalkers * 4));
+  if (!rc) rc = from_cuda(ensure(c->nch, S * kWalkers * 4));
+  if (!rc) rc = from_cuda(ensure(c->entcnt, S * 4));
+  if (!rc) rc = from_cuda(ensure(c->sel, S * 4));
+  if (!rc) rc = from_cuda(ensure(c->chars, S * (kWalkers + 1) * H));
+  if (rc) return rc;
+  rc = from_cuda(launch_xoff(d_x, m, false, 0, Rf, B, c->codemap(), c->sigma(), (uint32_t*)c->xoff_f.p,
+                             (uint8_t*)c->xcode.p, st));
+  if (!rc && rev)
+    rc = from_cuda(launch_xoff(d_x, m, true, padr, Rr, B, c->codemap(), c->sigma(), (uint32_t*)c->xoff_r.p, nullptr,
+                               st));
+  if (!rc) rc = from_cuda(cudaMemsetAsync(c->carry_f.p, 0, g.nblocks * Rf * 4, st));
+  if (!rc && rev) rc = from_cuda(cudaMemsetAsync(c->carry_r.p, 0, g.nblocks * Rr * 4, st));
+  if (!rc) rc = from_cuda(cudaMemsetAsync(c->len_acc(), 0, sizeof(unsigned long long), st));
+  if (rc) return rc;
+  FillJob jobs[2]{};
+  jobs[0].xoff = (const uint32_t*)c->xoff_f.p;
+  jobs[0].peq = (const uint32_t*)c->peq_f.p;
+  jobs[0].sigma_rows = c->sigma();
+  jobs[0].carry = (uint32_t*)c->carry_f.p;
+  jobs[0].T = (uint32_t*)c->T.p;
+  jobs[0].snap = (uint32_t*)c->snap_f.p;
+  jobs[0].snap_rb = (uint32_t)(H / B);
+  jobs[0].len_acc = c->len_acc();
+  jobs[0].R = Rf;
+  jobs[0].wpad = g.wpad;
+  jobs[0].nblocks_total = (uint32_t)g.nblocks;
+  if (rev) {
+    jobs[1] = jobs[0];
+    jobs[1].xoff = (const uint32_t*)c->xoff_r.p;
+    jobs[1].peq = (const uint32_t*)c->peq_r.p;
+    jobs[1].carry = (uint32_t*)c->carry_r.p;
+    jobs[1].T = nullptr;
+    jobs[1].snap = (uint32_t*)c->snap_r.p;
+    jobs[1].len_acc = nullptr;
+    jobs[1].R = Rr;
+  }
+  rc = run_fill(c, jobs, rev ? 2 : 1, true, st);
+  if (rc) return rc;
+  TraceArgs t{};
+  t.T = (const uint32_t*)c->T.p;
+  t.peq = (const uint32_t*)c->peq_f.p;
+  t.xcode = (const uint8_t*)c->xcode.p;
+  t.x = d_x;
+  t.snapF = (const uint32_t*)c->snap_f.p;
+  t.snapR = (const uint32_t*)c->snap_r.p;
+  t.L = c->len_acc();
+  t.ent = (uint32_t*)c->ent.p;
+  t.ent_cnt = (uint32_t*)c->entcnt.p;
+  t.ext = (uint32_t*)c->ext.p;
+  t.nch = (uint32_t*)c->nch.p;
+  t.chars = (uint8_t*)c->chars.p;
+  t.sel = (uint32_t*)c->sel.p;
+  t.colsum = (uint32_t*)c->colsum.p;
+  t.out = d_out;
+  t.out_len = (unsigned long long*)d_out_len;
+  t.out_cap = out_cap;
+  t.m = m;
+  t.n = n;
+  t.w = g.wq;
+  t.wpad = g.wpad;
+  t.R = Rf;
+  t.H = H;
+  t.S = S;
+  t.B = B;
+  t.status = c->status();
+  return from_cuda(launch_traceback(t, st));
+}
+
+}  // namespace lcs
+
+// ---- C ABI -----------------------------------------------------------------------------------------------------
+
+extern "C" int lcs_ctx_create(int device, lcs_ctx** out) {
+  if (!out) return LCS_ERR_INVALID;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return LCS_ERR_INVALID;
+  }
+  lcs_ctx* c = new (std::nothrow) lcs_ctx();
+  if (!c) return LCS_ERR_NOMEM;
+  c->device = device;
+  int rc = from_cuda(cudaSetDevice(device));
+  if (!rc) rc = from_cuda(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+  if (!rc) rc = from_cuda(ensure(c->small, kSmallBytes));
+  if (!rc) rc = from_cuda(cudaMemset(c->small.p, 0, kSmallBytes));
+  if (!rc) {
+    c->max_coop = fill_max_coop_blocks(device);
+    if (c->max_coop <= 0) rc = LCS_ERR_CUDA;
+  }
+  if (rc) {
+    lcs_ctx_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return LCS_OK;
+}
+
+extern "C" void lcs_ctx_destroy(lcs_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  c->release_all();
+  if (c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+extern "C" int lcs_ctx_sync(lcs_ctx* c) {
+  if (!c) return LCS_ERR_INVALID;
+  std::lock_guard<std::mutex> g(c->mu);
+  cudaSetDevice(c->device);
+  int rc = from_cuda(cudaStreamSynchronize(c->stream));
+  if (rc) return rc;
+  return take_status(c);
+}
+
+static cudaStream_t pick(lcs_ctx* c, void* s) { return s ? (cudaStream_t)s : c->stream; }
+
+extern "C" int lcs_length_dev(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, uint64_t n,
+                              uint64_t* d_out_len, void* stream) {
+  if (!c || !d_out_len || (m && !d_x) || (n && !d_y)) return LCS_ERR_INVALID;
+  if (m >= (1ull << 32) || n >= (1ull << 32)) return LCS_ERR_INVALID;
+  std::lock_guard<std::mutex> g(c->mu);
+  cudaSetDevice(c->device);
+  return run_length(c, d_x, m, d_y, n, d_out_len, pick(c, stream));
+}
+
+extern "C" int lcs_traceback_dev(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, uint64_t n,
+                                 uint8_t* d_out, uint64_t out_cap, uint64_t* d_out_len, void* stream) {
+  if (!c || !d_out_len || (m && !d_x) || (n && !d_y)) return LCS_ERR_INVALID;
+  if (m >= (1ull << 32) || n >= (1ull << 32)) return LCS_ERR_INVALID;
+  if (out_cap < std::min(m, n)) return LCS_ERR_CAPACITY;
+  if (std::min(m, n) > 0 && !d_out) return LCS_ERR_INVALID;
+  std::lock_guard<std::mutex> g(c->mu);
+  cudaSetDevice(c->device);
+  return run_traceback(c, d_x, m, d_y, n, d_out, out_cap, d_out_len, pick(c, stream));
+}
+
+// Copies host inputs into the context's device buffers.
+static int stage_inputs(lcs_ctx* c, const uint8_t* x, uint64_t m, const uint8_t* y, uint64_t n) {
+  int rc = from_cuda(ensure(c->x, std::max<uint64_t>(m, 1)));
+  if (!rc) rc = from_cuda(ensure(c->y, std::max<uint64_t>(n, 1)));
+  if (!rc && m) rc = from_cuda(cudaMemcpyAsync(c->x.p, x, m, cudaMemcpyHostToDevice, c->stream));
+  if (!rc && n) rc = from_cuda(cudaMemcpyAsync(c->y.p, y, n, cudaMemcpyHostToDevice, c->stream));
+  return rc;
+}
+
+extern "C" int lcs_length(lcs_ctx* c, const uint8_t* x, uint64_t m, const uint8_t* y, uint64_t n,
+                          uint64_t* out_len) {
+  if (!c || !out_len || (m && !x) || (n && !y)) return LCS_ERR_INVALID;
+  if (m >= (1ull << 32) || n >= (1ull << 32)) return LCS_ERR_INVALID;
+  std::lock_guard<std::mutex> g(c->mu);
+  cudaSetDevice(c->device);
+  *out_len = 0;
+  int rc = stage_inputs(c, x, m, y, n);
+  if (!rc) rc = run_length(c, (const uint8_t*)c->x.p, m, (const uint8_t*)c->y.p, n, c->out_len(), c->stream);
+  if (!rc) rc = from_cuda(cudaMemcpyAsync(c->host_word, c->out_len(), 8, cudaMemcpyDeviceToHost, c->stream));
+  if (!rc) rc = from_cuda(cudaStreamSynchronize(c->stream));
+  if (!rc) rc = take_status(c);
+  if (!rc) *out_len = *c->host_word;
+  return rc;
+}
+
+extern "C" int lcs_traceback(lcs_ctx* c, const uint8_t* x, uint64_t m, const uint8_t* y, uint64_t n, uint8_t* out,
+                             uint64_t out_cap, uint64_t* out_len) {
+  if (!c || !out_len || (m && !x) || (n && !y)) return LCS_ERR_INVALID;
+  if (m >= (1ull << 32) || n >= (1ull << 32)) return LCS_ERR_INVALID;
+  if (out_cap && !out) return LCS_ERR_INVALID;
+  std::lock_guard<std::mutex> g(c->mu);
+  cudaSetDevice(c->device);
+  *out_len = 0;
+  const uint64_t cap = std::max<uint64_t>(std::min(m, n), 1);
+  int rc = stage_inputs(c, x, m, y, n);
+  if (!rc) rc = from_cuda(ensure(c->out, cap));
+  if (!rc)
+    rc = run_traceback(c, (const uint8_t*)c->x.p, m, (const uint8_t*)c->y.p, n, (uint8_t*)c->out.p, cap,
+                       c->out_len(), c->stream);
+  if (!rc) rc = from_cuda(cudaMemcpyAsync(c->host_word, c->out_len(), 8, cudaMemcpyDeviceToHost, c->stream));
+  if (!rc) rc = from_cuda(cudaStreamSynchronize(c->stream));
+  if (!rc) rc = take_status(c);
+  if (rc) return rc;
+  const uint64_t L = *c->host_word;
+  *out_len = L;
+  if (L > out_cap) return LCS_ERR_CAPACITY;
+  if (L) rc = from_cuda(cudaMemcpy(out, c->out.p, L, cudaMemcpyDeviceToHost));
+  return rc;
+}

@@ -1,0 +1,54 @@
+// The context behind lcs_ctx*: streams, grow-only device buffers and the small control block.
+#pragma once
+
+#include <cstdint>
+#include <mutex>
+
+#include "lcs_internal.h"
+
+namespace lcs {
+
+struct DBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+cudaError_t ensure(DBuf& b, size_t bytes);
+void release(DBuf& b);
+int from_cuda(cudaError_t e);
+
+// Layout of the small control block (bytes).
+constexpr size_t kOffCodemap = 0;      // uint16_t[256]
+constexpr size_t kOffPresence = 512;   // uint32_t[8]
+constexpr size_t kOffSigma = 544;      // uint32_t
+constexpr size_t kOffLenAcc = 552;     // unsigned long long
+constexpr size_t kOffStatus = 576;     // DevStatus (16 B)
+constexpr size_t kOffOutLen = 608;     // uint64_t
+constexpr size_t kSmallBytes = 1024;
+
+}  // namespace lcs
+
+struct lcs_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int max_coop = 0;
+  uint32_t spin_limit = 1u << 22;
+  std::mutex mu;
+  lcs::DBuf small, x, y, out;
+  lcs::DBuf xoff_f, xoff_r, xcode, peq_f, peq_r, carry_f, carry_r, fv_f, fv_r, T, snap_f, snap_r;
+  lcs::DBuf colsum, ent, ext, nch, entcnt, sel, chars;
+  uint64_t host_word[1] = {0};
+
+  uint16_t* codemap() { return (uint16_t*)((char*)small.p + lcs::kOffCodemap); }
+  uint32_t* presence() { return (uint32_t*)((char*)small.p + lcs::kOffPresence); }
+  uint32_t* sigma() { return (uint32_t*)((char*)small.p + lcs::kOffSigma); }
+  unsigned long long* len_acc() { return (unsigned long long*)((char*)small.p + lcs::kOffLenAcc); }
+  lcs::DevStatus* status() { return (lcs::DevStatus*)((char*)small.p + lcs::kOffStatus); }
+  uint64_t* out_len() { return (uint64_t*)((char*)small.p + lcs::kOffOutLen); }
+
+  void release_all() {
+    lcs::DBuf* all[] = {&small, &x, &y, &out, &xoff_f, &xoff_r, &xcode, &peq_f, &peq_r, &carry_f, &carry_r,
+                        &fv_f, &fv_r, &T, &snap_f, &snap_r, &colsum, &ent, &ext, &nch, &entcnt, &sel, &chars};
+    for (lcs::DBuf* b : all) lcs::release(*b);
+  }
+};

@@ -1,0 +1,110 @@
+// Internal declarations shared by the CUDA translation units of liblcs.so.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/lcs.h"
+
+namespace lcs {
+
+// ---- fill kernel geometry ------------------------------------------------------------------------------------
+// One fill block = 4 warps (one per SM sub-partition); every lane owns one 32-bit word of the DP row, i.e. 32
+// columns of Y. A block therefore covers a stripe of 128 words = 4096 columns.
+constexpr int kFillWarps = 4;
+constexpr int kFillThreads = kFillWarps * 32;
+constexpr int kStripeWords = kFillThreads;
+constexpr int kRing = 256;              // slots of the shared-memory carry ring between neighbouring warps
+constexpr int kSigmaMax = 257;          // up to 256 byte values present in Y, plus the all-zero row
+constexpr int kPadRowblocks = 32;       // zero row-blocks in front of and behind every row-offset array
+
+// ---- device status word (latched errors) ---------------------------------------------------------------------
+constexpr uint32_t kStatTimeout = 1u;   // a bounded spin-wait expired
+constexpr uint32_t kStatInternal = 2u;  // internal consistency check failed (e.g. traced length != c[m,n])
+
+struct DevStatus {
+  uint32_t flags;   // kStat* bits
+  uint32_t abort;   // set together with a timeout: every waiting warp stops waiting
+  uint32_t where;   // diagnostic: which wait gave up
+  uint32_t pad;
+};
+
+// One DP problem for the fill kernel (a forward table, or the table of the reversed strings).
+struct FillJob {
+  const uint32_t* xoff;     // per padded row: byte offset of its symbol's row in the block's shared Peq stripe;
+                            // (kPadRowblocks + R + kPadRowblocks) * B entries
+  const uint32_t* peq;      // match masks [sigma row][wpad], row 'sigma' (the last) all zero
+  const uint32_t* sigma_rows;  // device word: rows of peq in use (present symbols + 1)
+  uint32_t* carry;          // [nblocks_total][R] hand-off slots, block b's last warp -> block b+1's first warp
+  uint32_t* T;              // traceback bitmap (carry-into vectors) or nullptr
+  uint32_t* snap;           // V snapshots [k][wpad] at the ends of row-blocks r with (r+1) % snap_rb == 0
+  uint32_t* final_v;        // V after the last row [wpad], or nullptr
+  unsigned long long* len_acc;  // += popc(~V) over the row (number of zero bits = c[last row, n]), or nullptr
+  uint64_t R;               // row-blocks
+  uint64_t wpad;            // words per row = lanes of the job (nblocks_total * 128)
+  uint32_t snap_rb;         // 0 = no snapshots
+  uint32_t nblocks_total;   // blocks of the job over all passes
+  uint32_t block0;          // first block of this launch (multi-pass)
+  uint32_t nblocks;         // blocks in this launch
+};
+
+struct FillArgs {
+  FillJob job[2];
+  uint32_t njobs;
+  DevStatus* status;
+  uint32_t spin_limit;      // iterations of a bounded wait before it gives up
+  uint32_t pad;
+};
+
+// ---- traceback segment walkers ---------------------------------------------------------------------------------
+constexpr int kWalkers = 32;            // walkers per segment (one warp)
+constexpr int kMaxSegments = 256;
+
+struct TraceArgs {
+  const uint32_t* T;        // forward bitmap (carry-into vectors, skewed chunk layout of the fill kernel)
+  const uint32_t* peq;      // forward match masks [sigma][wpad]
+  const uint8_t* xcode;     // symbol code per row (rows 1..m at index 0..m-1)
+  const uint8_t* x;         // the original X (bytes emitted into the LCS)
+  const uint32_t* snapF;    // forward V snapshots, index k-1 = row k*H
+  const uint32_t* snapR;    // reverse V snapshots, index S-k-1 = forward row k*H
+  const unsigned long long* L;  // c[m,n]
+  uint32_t* ent;            // [S][kWalkers] entry columns of the walkers
+  uint32_t* ent_cnt;        // [S] walkers per segment (kWalkers+1 = corridor overflow)
+  uint32_t* ext;            // [S][kWalkers] exit columns
+  uint32_t* nch;            // [S][kWalkers] symbols emitted by each walker
+  uint8_t* chars;           // [S][kWalkers + 1][H] emitted symbols in walk order (slot kWalkers: fallback)
+  uint32_t* sel;            // [S] selected walker per segment
+  uint32_t* colsum;         // scratch [2][S][w+1] word prefix popcounts
+  uint8_t* out;             // LCS output (capacity out_cap)
+  unsigned long long* out_len;
+  uint64_t out_cap;
+  uint64_t m, n, w, wpad, R, H, S;
+  uint32_t B;
+  DevStatus* status;
+};
+
+// ---- launchers (implemented in the .cu files) ------------------------------------------------------------------
+// prep
+cudaError_t launch_alphabet(const uint8_t* y, uint64_t n, uint32_t* presence8, uint16_t* codemap,
+                            uint32_t* sigma_rows, cudaStream_t st);
+cudaError_t launch_xoff(const uint8_t* x, uint64_t m, bool reverse, uint64_t pad_front, uint64_t R, uint32_t B,
+                        const uint16_t* codemap, const uint32_t* sigma_rows, uint32_t* xoff, uint8_t* xcode,
+                        cudaStream_t st);
+cudaError_t launch_peq(const uint8_t* y, uint64_t n, bool reverse, uint64_t wpad, const uint16_t* codemap,
+                       uint32_t* peq, cudaStream_t st);
+// fill
+int fill_max_coop_blocks(int device);
+cudaError_t launch_fill(const FillArgs& a, uint32_t B, bool traceback, cudaStream_t st);
+size_t fill_smem_bytes();
+// length meet-in-the-middle combine: L = n - min_j (pf(j) + pr(n-j))
+cudaError_t launch_combine(const uint32_t* vf, const uint32_t* vr, uint64_t n, uint64_t w,
+                           uint32_t* colsum, unsigned long long* out_len, cudaStream_t st);
+// traceback
+cudaError_t launch_traceback(const TraceArgs& t, cudaStream_t st);
+// batch
+struct BatchPlan;
+// misc
+cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
+
+}  // namespace lcs

@@ -1,0 +1,292 @@
+// Traceback (paper §I.D, Print-LCS) over the 1-bit direction bitmap of the fill kernel, made parallel.
+//
+// Print-LCS walks from (m, n) towards row 0: DIAG on a match (emit x_i), else UP when c[i-1,j] >= c[i,j-1],
+// else LEFT. At row i the walk moves left past LEFT cells to the first column c <= j that is a match or an UP
+// cell, then steps to row i-1 (to column c-1 on a match, to c otherwise). That is one word scan per row here.
+//
+// The rows are cut into S segments of H rows; every segment is walked at once by a warp of up to 32 walkers.
+// Where the true path enters a segment is unknown until the segment below is done, but it must lie on an optimal
+// path, so it is one of the columns j of the segment's bottom row with c[i,j] + LCS(X[i+1..m], Y[j+1..n]) = c[m,n]
+// ("corridor" columns). The prefix lengths c[i,.] come from V snapshots of the forward fill, the suffix lengths
+// from V snapshots of the same fill run on the reversed strings. Every corridor column gets a walker; a short
+// chain pass then follows the true path from (m, n) segment by segment, picking in each segment the walker whose
+// entry is the exit of the segment below (or walking the segment itself when the corridor had more columns than
+// walkers). The chosen walkers' symbols are finally copied to the output in order. The result is exactly the walk
+// of Print-LCS; only the order of the work differs.
+#include "lcs_internal.h"
+
+namespace lcs {
+
+namespace {
+
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+
+// ---- word prefix popcounts of V rows ------------------------------------------------------------------------
+// For a V row (bit j-1 of the row = 1 - (c[i,j] - c[i,j-1])), pre[q] = ones among the first 32*q bits.
+// One block per row; each thread scans a contiguous run of words.
+__device__ void block_prefix_popc(const uint32_t* __restrict__ v, uint64_t w, uint32_t* __restrict__ pre) {
+  __shared__ uint32_t part[1024];
+  const uint32_t nt = blockDim.x, tid = threadIdx.x;
+  const uint64_t per = (w + nt - 1) / nt;
+  const uint64_t q0 = tid * per, q1 = (q0 + per < w) ? q0 + per : w;
+  uint32_t s = 0;
+  for (uint64_t q = q0; q < q1; ++q) s += __popc(v[q]);
+  part[tid] = s;
+  __syncthreads();
+  for (uint32_t off = 1; off < nt; off <<= 1) {  // Hillis-Steele inclusive scan over thread totals
+    const uint32_t add = tid >= off ? part[tid - off] : 0u;
+    __syncthreads();
+    part[tid] += add;
+    __syncthreads();
+  }
+  uint32_t run = part[tid] - s;
+  for (uint64_t q = q0; q < q1; ++q) {
+    pre[q] = run;
+    run += __popc(v[q]);
+  }
+  if (tid == nt - 1) pre[w] = part[tid];
+  __syncthreads();
+}
+
+// ones among the first x bits of the row
+__device__ __forceinline__ uint32_t ones_prefix(const uint32_t* v, const uint32_t* pre, uint64_t x) {
+  const uint64_t q = x >> 5;
+  const uint32_t k = (uint32_t)(x & 31);
+  return pre[q] + (k ? __popc(v[q] & ((1u << k) - 1u)) : 0u);
+}
+
+// ---- meet-in-the-middle length: L = n - min_j (ones_f(j) + ones_r(n - j)) -----------------------------------
+__global__ void k_combine_pre(const uint32_t* vf, const uint32_t* vr, uint64_t w, uint32_t* colsum) {
+  block_prefix_popc(blockIdx.x == 0 ? vf : vr, w, colsum + blockIdx.x * (w + 1));
+  if (blockIdx.x == 0 && threadIdx.x == 0) colsum[2 * (w + 1)] = 0xFFFFFFFFu;  // running minimum
+}
+
+__global__ void k_combine_min(const uint32_t* vf, const uint32_t* vr, uint64_t n, uint64_t w, uint32_t* colsum) {
+  const uint32_t* pf = colsum;
+  const uint32_t* pr = colsum + (w + 1);
+  uint32_t best = 0xFFFFFFFFu;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j <= n; j += stride) {
+    const uint32_t s = ones_prefix(vf, pf, j) + ones_prefix(vr, pr, n - j);
+    best = s < best ? s : best;
+  }
+  best = __reduce_min_sync(kFull, best);
+  if ((threadIdx.x & 31) == 0) atomicMin(colsum + 2 * (w + 1), best);
+}
+
+__global__ void k_combine_fin(const uint32_t* colsum, uint64_t n, uint64_t w, unsigned long long* out_len) {
+  *out_len = (unsigned long long)(n - colsum[2 * (w + 1)]);
+}
+
+// ---- corridors -------------------------------------------------------------------------------------------------
+// Boundary k (1..S-1) is forward row k*H, the bottom row of segment k-1.
+__global__ void k_corr_pre(TraceArgs a) {
+  const uint64_t k = blockIdx.x + 1;
+  const uint64_t wp1 = a.w + 1;
+  block_prefix_popc(a.snapF + (k - 1) * a.wpad, a.w, a.colsum + (2 * (k - 1)) * wp1);
+  block_prefix_popc(a.snapR + (a.S - k - 1) * a.wpad, a.w, a.colsum + (2 * (k - 1) + 1) * wp1);
+}
+
+__global__ void k_corr_cols(TraceArgs a) {
+  const uint64_t k = blockIdx.y + 1;
+  const uint64_t wp1 = a.w + 1;
+  const uint32_t* vf = a.snapF + (k - 1) * a.wpad;
+  const uint32_t* vr = a.snapR + (a.S - k - 1) * a.wpad;
+  const uint32_t* pf = a.colsum + (2 * (k - 1)) * wp1;
+  const uint32_t* pr = a.colsum + (2 * (k - 1) + 1) * wp1;
+  const uint64_t target = a.n - *a.L;  // c[i,j] + suffix = n - (ones_f + ones_r); optimal when that sum = n - L
+  const uint64_t s = k - 1;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j <= a.n; j += stride) {
+    const uint32_t sum = ones_prefix(vf, pf, j) + ones_prefix(vr, pr, a.n - j);
+    if (sum == target) {
+      const uint32_t slot = atomicAdd(&a.ent_cnt[s], 1u);
+      if (slot < (uint32_t)kWalkers) a.ent[s * kWalkers + slot] = (uint32_t)j;
+    }
+  }
+}
+
+// ---- the walk of one segment -------------------------------------------------------------------------------------
+// Direction bit of cell (i, c): bit c%32 of T-frame word c/32 of row i holds c[i,c] - c[i-1,c] (the carry into
+// column c+1's bit); 0 = UP, 1 = LEFT on a mismatch. Match bit of (i, c): bit (c-1)%32 of Peq word (c-1)/32.
+__device__ __forceinline__ uint32_t t_word(const TraceArgs& a, uint64_t i, uint64_t Q) {
+  const uint64_t r = (i - 1) >> 3, b = (i - 1) & 7;  // B = 8
+  const uint64_t chunk = (Q >> 5) * (a.R + 31) + r + (Q & 31);
+  return a.T[chunk * 256 + (b >> 2) * 128 + (Q & 31) * 4 + (b & 3)];
+}
+
+__device__ __forceinline__ uint32_t p_word(const TraceArgs& a, uint32_t code, int64_t q) {
+  return q < 0 ? 0u : __ldg(a.peq + (uint64_t)code * a.wpad + (uint64_t)q);
+}
+
+// Walks rows hi..lo+1 from column e; returns the exit column (at row lo); writes emitted symbols to out_chars.
+__device__ uint64_t walk_segment(const TraceArgs& a, uint64_t hi, uint64_t lo, uint64_t e, uint8_t* out_chars,
+                                 uint32_t* out_cnt) {
+  uint64_t i = hi, j = e;
+  uint32_t cnt = 0;
+  while (i > lo && j > 0) {
+    const uint32_t code = a.xcode[i - 1];
+    int64_t Q = (int64_t)(j >> 5);
+    uint32_t mask = kFull >> (31 - (uint32_t)(j & 31));
+    uint32_t pm = 0, stop = 0;
+    for (;;) {
+      const uint32_t dv = t_word(a, i, (uint64_t)Q);
+      pm = (p_word(a, code, Q) << 1) | (p_word(a, code, Q - 1) >> 31);
+      stop = (pm | ~dv) & mask;
+      if (Q == 0) stop &= ~1u;  // column 0 is the border
+      if (stop || Q == 0) break;
+      --Q;
+      mask = kFull;
+    }
+    if (!stop) {
+      j = 0;
+      break;
+    }
+    const uint32_t bit = 31u - __clz(stop);
+    const uint64_t c = ((uint64_t)Q << 5) + bit;
+    if ((pm >> bit) & 1u) {
+      out_chars[cnt++] = a.x[i - 1];
+      j = c - 1;
+    } else {
+      j = c;
+    }
+    --i;
+  }
+  *out_cnt = cnt;
+  return j;
+}
+
+__global__ void k_walk(TraceArgs a) {
+  const uint64_t s = blockIdx.x;
+  const uint32_t k = threadIdx.x;
+  const uint32_t cnt = a.ent_cnt[s];
+  if (k >= (cnt < (uint32_t)kWalkers ? cnt : (uint32_t)kWalkers)) return;
+  const uint64_t lo = s * a.H, hi = (s + 1) * a.H < a.m ? (s + 1) * a.H : a.m;
+  const uint64_t e = a.ent[s * kWalkers + k];
+  uint32_t nc = 0;
+  const uint64_t x = walk_segment(a, hi, lo, e, a.chars + (s * (kWalkers + 1) + k) * a.H, &nc);
+  a.ext[s * kWalkers + k] = (uint32_t)x;
+  a.nch[s * kWalkers + k] = nc;
+}
+
+// Follows the true path from (m, n) down the segments (one warp; all entries and exits staged in shared memory).
+__global__ void k_chain(TraceArgs a) {
+  extern __shared__ uint32_t sm[];
+  uint32_t* ent = sm;                         // [S][kWalkers]
+  uint32_t* ext = sm + a.S * kWalkers;        // [S][kWalkers]
+  uint32_t* cnt = sm + 2 * a.S * kWalkers;    // [S]
+  const uint32_t lane = threadIdx.x;
+  for (uint64_t i = lane; i < a.S * kWalkers; i += 32) {
+    ent[i] = a.ent[i];
+    ext[i] = a.ext[i];
+  }
+  for (uint64_t i = lane; i < a.S; i += 32) cnt[i] = a.ent_cnt[i];
+  __syncwarp();
+  uint64_t e = a.n;
+  for (int64_t s = (int64_t)a.S - 1; s >= 0; --s) {
+    const uint32_t c = cnt[s] < (uint32_t)kWalkers ? cnt[s] : (uint32_t)kWalkers;
+    const bool hit = lane < c && ent[s * kWalkers + lane] == (uint32_t)e;
+    const uint32_t b = __ballot_sync(kFull, hit);
+    if (b) {
+      const uint32_t k = __ffs(b) - 1;
+      if (lane == 0) a.sel[s] = k;
+      e = ext[s * kWalkers + k];
+    } else {
+      // the entry is not among the walkers (corridor wider than the warp): walk the segment here
+      uint64_t x = 0;
+      if (lane == 0) {
+        const uint64_t lo = (uint64_t)s * a.H, hi = ((uint64_t)s + 1) * a.H < a.m ? ((uint64_t)s + 1) * a.H : a.m;
+        uint32_t nc = 0;
+        x = walk_segment(a, hi, lo, e, a.chars + ((uint64_t)s * (kWalkers + 1) + kWalkers) * a.H, &nc);
+        a.sel[s] = kWalkers;
+        a.ent_cnt[s] = 0x80000000u | nc;  // fallback count, read by k_finalize
+      }
+      e = __shfl_sync(kFull, x, 0);
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t seg_count(const TraceArgs& a, uint64_t s) {
+  const uint32_t k = a.sel[s];
+  if (k == (uint32_t)kWalkers) return a.ent_cnt[s] & 0x7FFFFFFFu;
+  return a.nch[s * kWalkers + k];
+}
+
+// Block s copies its selected walker's symbols (walk order = reverse output order) to their place in the output.
+__global__ void k_finalize(TraceArgs a) {
+  __shared__ uint32_t red[32];
+  const uint64_t s = blockIdx.x;
+  uint32_t before = 0, total = 0;
+  for (uint64_t t = threadIdx.x; t < a.S; t += blockDim.x) {
+    const uint32_t c = seg_count(a, t);
+    total += c;
+    if (t < s) before += c;
+  }
+  before = __reduce_add_sync(kFull, before);
+  total = __reduce_add_sync(kFull, total);
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = before;
+    red[16 + (threadIdx.x >> 5)] = total;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t b = 0, tt = 0;
+    for (uint32_t w = 0; w < blockDim.x / 32; ++w) {
+      b += red[w];
+      tt += red[16 + w];
+    }
+    red[0] = b;
+    red[16] = tt;
+  }
+  __syncthreads();
+  before = red[0];
+  total = red[16];
+  const uint32_t k = a.sel[s];
+  const uint32_t c = seg_count(a, s);
+  const uint8_t* src = a.chars + (s * (kWalkers + 1) + k) * a.H;
+  const bool fits = (uint64_t)before + c <= a.out_cap;  // always true unless the walks were inconsistent
+  if (fits)
+    for (uint32_t t = threadIdx.x; t < c; t += blockDim.x) a.out[before + c - 1 - t] = src[t];
+  if (threadIdx.x == 0 && (!fits || (s == 0 && (unsigned long long)total != *a.L)))
+    atomicOr(&a.status->flags, kStatInternal);
+  if (s == 0 && threadIdx.x == 0) *a.out_len = total;
+}
+
+// Segment S-1 starts at (m, n); segments with no boundary corridor data (S == 1) likewise.
+__global__ void k_seed_last(TraceArgs a) {
+  a.ent[(a.S - 1) * kWalkers] = (uint32_t)a.n;
+  a.ent_cnt[a.S - 1] = 1;
+}
+
+}  // namespace
+
+cudaError_t launch_combine(const uint32_t* vf, const uint32_t* vr, uint64_t n, uint64_t w, uint32_t* colsum,
+                           unsigned long long* out_len, cudaStream_t st) {
+  k_combine_pre<<<2, 1024, 0, st>>>(vf, vr, w, colsum);
+  uint64_t blocks = (n + 1 + 255) / 256;
+  if (blocks > 2048) blocks = 2048;
+  k_combine_min<<<(unsigned)blocks, 256, 0, st>>>(vf, vr, n, w, colsum);
+  k_combine_fin<<<1, 1, 0, st>>>(colsum, n, w, out_len);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_traceback(const TraceArgs& a, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(a.ent_cnt, 0, a.S * sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  k_seed_last<<<1, 1, 0, st>>>(a);
+  if (a.S > 1) {
+    k_corr_pre<<<(unsigned)(a.S - 1), 1024, 0, st>>>(a);
+    uint64_t gx = (a.n + 1 + 255) / 256;
+    if (gx > 1024) gx = 1024;
+    k_corr_cols<<<dim3((unsigned)gx, (unsigned)(a.S - 1)), 256, 0, st>>>(a);
+  }
+  k_walk<<<(unsigned)a.S, kWalkers, 0, st>>>(a);
+  const size_t chain_smem = (size_t)(2 * a.S * kWalkers + a.S) * sizeof(uint32_t);
+  e = cudaFuncSetAttribute(k_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chain_smem);
+  if (e != cudaSuccess) return e;
+  k_chain<<<1, 32, chain_smem, st>>>(a);
+  k_finalize<<<(unsigned)a.S, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace lcs

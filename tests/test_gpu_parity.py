@@ -1,0 +1,108 @@
+"""CUDA path vs the CPU oracle, element by element (length and LCS string must be identical)."""
+
+import os
+import random
+
+import numpy as np
+import pytest
+
+from paper_1306_4627_gb300 import gen
+from tests.conftest import read_golden_cases
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "clrs_tiebreak.txt")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1306_4627_gb300 import lcs
+    c = lcs.Context(0)
+    yield c
+    c.close()
+
+
+def check_pair(ctx, oracle, x, y, traceback=True):
+    x = np.ascontiguousarray(x, dtype=np.uint8)
+    y = np.ascontiguousarray(y, dtype=np.uint8)
+    L = oracle.lcs_length(x, y)
+    assert ctx.length(x, y) == L, (len(x), len(y))
+    if traceback:
+        s = ctx.traceback(x, y)
+        assert s == oracle.lcs_traceback(x, y), (len(x), len(y))
+
+
+def test_golden_cases(ctx, oracle):
+    cases, _ = read_golden_cases(GOLDEN)
+    for x, y, L, s in cases:
+        assert ctx.length(x, y) == L
+        assert ctx.traceback(x, y) == s
+
+
+def test_empty(ctx):
+    assert ctx.length(b"", b"ACGT") == 0
+    assert ctx.length(b"ACGT", b"") == 0
+    assert ctx.traceback(b"", b"") == b""
+    assert ctx.traceback(b"AC", b"") == b""
+
+
+@pytest.mark.parametrize("sigma", [2, 4, 20, 256])
+def test_random_small(ctx, oracle, sigma):
+    rng = random.Random(sigma)
+    alpha = {2: b"AB", 4: gen.DNA, 20: gen.PROTEIN, 256: gen.BYTES}[sigma]
+    for k in range(40):
+        m, n = rng.randint(1, 300), rng.randint(1, 300)
+        x = gen.random_string(1000 * sigma + 2 * k, m, alpha)
+        y = gen.random_string(1000 * sigma + 2 * k + 1, n, alpha)
+        check_pair(ctx, oracle, x, y)
+
+
+@pytest.mark.parametrize("m", [1, 7, 8, 9, 31, 32, 33, 1023, 1024, 1025])
+@pytest.mark.parametrize("n", [1, 31, 32, 33, 63, 64, 4095, 4096, 4097])
+def test_edge_shapes(ctx, oracle, m, n):
+    x, y = gen.pair_uniform(m, n, 4, seed=m * 10007 + n)
+    check_pair(ctx, oracle, x, y)
+
+
+def test_multi_block_columns(ctx, oracle):
+    # n spans several 4096-column blocks (global carry hand-off) and a ragged last word
+    for m, n in [(700, 9000), (2050, 12289), (64, 20000)]:
+        x, y = gen.pair_uniform(m, n, 4, seed=m + n)
+        check_pair(ctx, oracle, x, y)
+
+
+def test_identical_and_disjoint(ctx):
+    x = gen.random_string(3, 5000, gen.DNA)
+    assert ctx.length(x, x) == 5000
+    assert ctx.traceback(x, x) == x.tobytes()
+    a = gen.random_string(4, 3000, b"AC")
+    b = gen.random_string(5, 3100, b"GT")
+    assert ctx.length(a, b) == 0
+    assert ctx.traceback(a, b) == b""
+
+
+def test_single_pair_2048_dna(ctx, oracle):
+    x, y = gen.pair_uniform(2048, 2048, 4, seed=gen.BASE_SEED + 0)
+    check_pair(ctx, oracle, x, y)
+
+
+@pytest.mark.parametrize("variant", ["uniform", "mutated"])
+def test_pair_16384(ctx, oracle, variant):
+    if variant == "uniform":
+        x, y = gen.pair_uniform(16384, 16384, 4, seed=77)
+    else:
+        x, y = gen.pair_mutated(16384, 4, seed=78)
+    check_pair(ctx, oracle, x, y)
+
+
+@pytest.mark.parametrize("sigma", [20, 256])
+def test_pair_large_alphabets(ctx, oracle, sigma):
+    x, y = gen.pair_uniform(5000, 7000, sigma, seed=sigma)
+    check_pair(ctx, oracle, x, y)
+
+
+def test_capacity_error(ctx):
+    from paper_1306_4627_gb300 import lcs
+    with pytest.raises(lcs.LCSError) as e:
+        ctx.traceback(b"ACGTACGT", b"ACGTTTTT", out_cap=2)
+    assert e.value.code == lcs.ERR_CAPACITY
