@@ -1,0 +1,313 @@
+"""Benchmark of the LCS hot path on GB300: one step = LCS length + traceback of one long pair.
+
+Workload: X and Y of m = n = 65536 uniform i.i.d. DNA symbols (seeded), the LCS length and the LCS string by the
+paper's tie-break (UP when c[i-1,j] >= c[i,j-1]); every step runs all stages (alphabet and match masks, the table
+fill writing the 1-bit direction bitmap, the parallel traceback). Metric: GCUPS = m*n / seconds / 1e9.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line. `value` is timed on the device with the inputs resident in HBM (CUDA events around each step
+on the launching stream; the step writes a 537 MB bitmap, more than the 129 MB L2, and an explicit L2 flush runs
+between timed steps outside the events). `e2e` times the same step through the host-buffer call lcs_traceback
+(host->device copy of X and Y, device->host copy of the result, inside the timed region). `--impl reference` times
+the CPU oracle instead, on the host cores, on a bounded sample of the same workload (the first rows of X).
+Under torchrun (N > 1) every rank runs its own replica of the step on its own GPU (the single-pair path does not
+shard); value = total cells of all ranks / the slowest rank's time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+M = N = 65536
+SIGMA = 4
+WORKLOAD = "single pair, X and Y uniform DNA (sigma=4), m=n=65536: LCS length + traceback string"
+METRIC = "LCS GCUPS on 1 GB300 vs int-ALU roofline; serve p50/p99 latency vs per-pair"
+HBM_FALLBACK_GBS = 6800.0
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [v.strip() for v in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names[1:], start=5):
+                if p[k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_sample(x, y, budget_rows: int):
+    """Times the oracle (LCS-length + Print-LCS) on the first budget_rows rows of X against all of Y."""
+    from oracle import oracle
+    oracle.build()
+    xs = x[:budget_rows]
+    t0 = time.perf_counter()
+    s = oracle.lcs_traceback(xs, y)
+    dt = time.perf_counter() - t0
+    return len(xs) * len(y) / dt / 1e9, dt, len(s)
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        if rank != 0:
+            dist.barrier()
+            return
+    from paper_1306_4627_gb300 import gen
+    x, y = gen.pair_uniform(M, N, SIGMA, seed=gen.BASE_SEED + 1)
+    rows = args.ref_rows
+    for _ in range(args.warmup):
+        cpu_oracle_sample(x, y, max(8, rows // 8))
+    times = []
+    for _ in range(args.steps):
+        g, dt, _ = cpu_oracle_sample(x, y, rows)
+        times.append(dt)
+    cells = rows * N
+    value = cells / float(np.mean(times)) / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(times)) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "m": M, "n": N, "sigma": SIGMA},
+        "cpu_baseline": {"value": value, "unit": "GCUPS", "cores": 1, "kind": "oracle",
+                         "sample": f"first {rows} rows of X against all {N} columns of Y per step "
+                                   f"({cells:.3g} cells), LCS-length with table b + Print-LCS"},
+        "e2e": {"value": value, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def flush_l2(buf):
+    buf.add_(1)  # writes 256 MiB (> 129 MB L2)
+
+
+def run_gpu(args):
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1306_4627_gb300 import gen, lcs
+
+    x_np, y_np = gen.pair_uniform(M, N, SIGMA, seed=gen.BASE_SEED + 1)
+    dev = torch.device("cuda", local)
+    x = torch.from_numpy(x_np.copy()).to(dev)
+    y = torch.from_numpy(y_np.copy()).to(dev)
+    out = torch.empty(min(M, N), dtype=torch.uint8, device=dev)
+    out_len = torch.zeros(1, dtype=torch.int64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)
+    ctx = lcs.Context(local)
+    stream = torch.cuda.Stream(device=dev)
+    ctx.set_profiling(True)
+
+    def step():
+        ctx.traceback_dev(x, y, out, out_len, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+            flush_l2(flush)
+    torch.cuda.synchronize()
+    ctx.sync()
+    L = int(out_len.item())
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    fill_ms, trace_ms, prep_ms = [], [], []
+    sampler = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            evs[k][0].record(stream)
+            step()
+            evs[k][1].record(stream)
+            p = ctx.last_profile()  # waits for this step's stage events
+            fill_ms.append(p["fill_ms"])
+            trace_ms.append(p["trace_ms"])
+            prep_ms.append(p["prep_ms"])
+            flush_l2(flush)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ctx.sync()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    t_ms = float(np.mean(step_ms))
+    if dist is not None:
+        tt = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+        dist.barrier()
+    cells = M * N
+    value = ws * cells / (t_ms * 1e-3) / 1e9
+
+    # end to end through the host-buffer call (pinned host inputs, result copied back inside the timed region)
+    xh = torch.from_numpy(x_np.copy()).pin_memory()
+    yh = torch.from_numpy(y_np.copy()).pin_memory()
+    ctx.set_profiling(False)
+    e2e_times = []
+    s_out = b""
+    for k in range(0 if args.no_e2e else args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s_out = ctx.traceback(xh.numpy(), yh.numpy())
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            e2e_times.append(dt)
+    e2e_s = float(np.mean(e2e_times)) if e2e_times else float("nan")
+    if dist is not None:
+        tt = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    assert args.no_e2e or len(s_out) == L
+
+    # roofline of the dominant kernel (the fill): algorithmic bytes = the 1-bit-per-cell direction bitmap
+    hbm, src = peaks()
+    f_ms = float(np.mean(fill_ms))
+    alg_bytes = cells / 8
+    achieved = alg_bytes / (f_ms * 1e-3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "fill_traffic.json")
+    if os.path.exists(tfile):
+        try:
+            with open(tfile) as f:
+                traffic = json.load(f).get("bytes_per_launch_65536")
+        except Exception:
+            traffic = None
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        g, dt, _ = cpu_oracle_sample(x_np, y_np, args.cpu_rows)
+        cpu = {"value": g, "unit": "GCUPS", "cores": 1, "kind": "oracle",
+               "sample": f"first {args.cpu_rows} rows of X against all {N} columns of Y "
+                         f"({args.cpu_rows * N:.3g} cells, {dt:.1f} s), LCS-length with table b + Print-LCS"}
+    launches_per_step = 13
+    line = {
+        "metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "m": M, "n": N, "sigma": SIGMA, "seed": gen.BASE_SEED + 1,
+                   "lcs_length": L, "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
+                   "l2": "explicit 256 MiB L2 flush between timed steps (outside the events); each step also "
+                         "writes a 537 MB bitmap"},
+        "stages_ms": {"prep": float(np.mean(prep_ms)), "fill": f_ms, "trace": float(np.mean(trace_ms))},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": traffic, "kernel": "k_fill<8,true>", "peak_source": src,
+                     "note": "algorithmic bytes = m*n/8 (1-bit direction bitmap) per launch"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": ws * cells / e2e_s / 1e9, "unit": "GCUPS", "h2d_bytes_per_step": M + N,
+                "d2h_bytes_per_step": 8 + L},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    global M, N
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-rows", type=int, default=16384)
+    ap.add_argument("--ref-rows", type=int, default=2048)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--m", type=int, default=M, help="rows (profiling of smaller cases only)")
+    ap.add_argument("--n", type=int, default=N, help="columns (profiling of smaller cases only)")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    M, N = args.m, args.n
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -66,6 +66,25 @@ LCS_API void lcs_ctx_destroy(lcs_ctx* ctx);
  * (LCS_ERR_TIMEOUT, LCS_ERR_INTERNAL) or LCS_OK. */
 LCS_API int lcs_ctx_sync(lcs_ctx* ctx);
 
+/* ---- stage timing ----------------------------------------------------------------------------------------------
+ * The paper times its method with omp_get_wtime around the whole computation (§II.A, steps 6 and 21, EXEC_TIME).
+ * Here every stage of the last length/traceback call is timed with CUDA events recorded on the call's stream. */
+typedef struct lcs_profile {
+  double prep_ms;        /* alphabet, match masks and per-row symbol offsets */
+  double fill_ms;        /* the table fill kernel (all rows; both tables when the reversed strings run too) */
+  double trace_ms;       /* corridors, segment walks, chain and output assembly (0 for length-only calls) */
+  double total_ms;       /* first stage start to last stage end */
+  uint64_t fill_blocks;  /* thread blocks of the fill launch */
+  uint64_t cells;        /* m * n of the call */
+} lcs_profile;
+
+/* enable != 0 makes later calls record stage events (a few microseconds of overhead per call). */
+LCS_API int lcs_ctx_set_profiling(lcs_ctx* ctx, int enable);
+
+/* Waits for the last profiled call's events and fills *out. LCS_ERR_INVALID when profiling is off or no call was
+ * profiled yet. */
+LCS_API int lcs_ctx_last_profile(lcs_ctx* ctx, lcs_profile* out);
+
 /* ---- length (paper §I.C, LCS-length; returns c[m,n]) --------------------------------------------------------- */
 
 /* Host buffers x[0..m), y[0..n); writes c[m,n] to *out_len. Blocking. m = 0 or n = 0 gives 0. Errors:

@@ -135,6 +135,7 @@ int run_length(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, u
   const uint64_t Rf = (mt + B - 1) / B;
   const uint64_t padr = split ? (B - mb % B) % B : 0;
   const uint64_t Rr = split ? (mb + padr) / B : 0;
+  c->mark(0, st);
   int rc = prep_y(c, d_y, n, g, split, st);
   if (rc) return rc;
   rc = from_cuda(ensure(c->xoff_f, (Rf + 2 * kPadRowblocks) * B * 4));
@@ -172,12 +173,21 @@ int run_length(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, u
     jobs[1].len_acc = nullptr;
     jobs[1].R = Rr;
   }
+  c->mark(1, st);
   rc = run_fill(c, jobs, split ? 2 : 1, false, st);
+  c->mark(2, st);
   if (rc) return rc;
   if (split)
-    return from_cuda(launch_combine((const uint32_t*)c->fv_f.p, (const uint32_t*)c->fv_r.p, n, g.wq,
-                                    (uint32_t*)c->colsum.p, (unsigned long long*)d_out, st));
-  return from_cuda(cudaMemcpyAsync(d_out, c->len_acc(), sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
+    rc = from_cuda(launch_combine((const uint32_t*)c->fv_f.p, (const uint32_t*)c->fv_r.p, n, g.wq,
+                                  (uint32_t*)c->colsum.p, (unsigned long long*)d_out, st));
+  else
+    rc = from_cuda(cudaMemcpyAsync(d_out, c->len_acc(), sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
+  c->mark(3, st);
+  c->prof_valid = c->prof;
+  c->prof_trace = false;
+  c->prof_blocks = g.nblocks * (split ? 2 : 1);
+  c->prof_cells = m * n;
+  return rc;
 }
 
 int run_traceback(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, uint64_t n, uint8_t* d_out,
@@ -195,6 +205,7 @@ int run_traceback(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y
   const uint64_t Rr = rev ? (S * H) / B : 0;
   const uint64_t nwarps = g.nblocks * kFillWarps;
   const size_t t_bytes = (size_t)nwarps * (Rf + 31) * 32 * B * 4;
+  c->mark(0, st);
   int rc = prep_y(c, d_y, n, g, rev, st);
   if (rc) return rc;
   rc = from_cuda(ensure(c->T, t_bytes));
@@ -244,7 +255,9 @@ int run_traceback(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y
     jobs[1].len_acc = nullptr;
     jobs[1].R = Rr;
   }
+  c->mark(1, st);
   rc = run_fill(c, jobs, rev ? 2 : 1, true, st);
+  c->mark(2, st);
   if (rc) return rc;
   TraceArgs t{};
   t.T = (const uint32_t*)c->T.p;
@@ -273,7 +286,13 @@ int run_traceback(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y
   t.S = S;
   t.B = B;
   t.status = c->status();
-  return from_cuda(launch_traceback(t, st));
+  rc = from_cuda(launch_traceback(t, st));
+  c->mark(3, st);
+  c->prof_valid = c->prof;
+  c->prof_trace = true;
+  c->prof_blocks = g.nblocks * (rev ? 2 : 1);
+  c->prof_cells = m * n;
+  return rc;
 }
 
 }  // namespace lcs
@@ -312,6 +331,8 @@ extern "C" void lcs_ctx_destroy(lcs_ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   c->release_all();
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
   if (c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -326,6 +347,41 @@ extern "C" int lcs_ctx_sync(lcs_ctx* c) {
 }
 
 static cudaStream_t pick(lcs_ctx* c, void* s) { return s ? (cudaStream_t)s : c->stream; }
+
+extern "C" int lcs_ctx_set_profiling(lcs_ctx* c, int enable) {
+  if (!c) return LCS_ERR_INVALID;
+  std::lock_guard<std::mutex> g(c->mu);
+  cudaSetDevice(c->device);
+  if (enable && !c->ev[0])
+    for (auto& e : c->ev) {
+      int rc = from_cuda(cudaEventCreate(&e));
+      if (rc) return rc;
+    }
+  c->prof = enable != 0;
+  c->prof_valid = false;
+  return LCS_OK;
+}
+
+extern "C" int lcs_ctx_last_profile(lcs_ctx* c, lcs_profile* out) {
+  if (!c || !out) return LCS_ERR_INVALID;
+  std::lock_guard<std::mutex> g(c->mu);
+  if (!c->prof || !c->prof_valid) return LCS_ERR_INVALID;
+  cudaSetDevice(c->device);
+  int rc = from_cuda(cudaEventSynchronize(c->ev[3]));
+  if (rc) return rc;
+  float t01 = 0, t12 = 0, t23 = 0, t03 = 0;
+  cudaEventElapsedTime(&t01, c->ev[0], c->ev[1]);
+  cudaEventElapsedTime(&t12, c->ev[1], c->ev[2]);
+  cudaEventElapsedTime(&t23, c->ev[2], c->ev[3]);
+  cudaEventElapsedTime(&t03, c->ev[0], c->ev[3]);
+  out->prep_ms = t01;
+  out->fill_ms = t12;
+  out->trace_ms = c->prof_trace ? t23 : 0.0;
+  out->total_ms = t03;
+  out->fill_blocks = c->prof_blocks;
+  out->cells = c->prof_cells;
+  return LCS_OK;
+}
 
 extern "C" int lcs_length_dev(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, uint64_t n,
                               uint64_t* d_out_len, void* stream) {

@@ -38,6 +38,13 @@ struct lcs_ctx {
   lcs::DBuf xoff_f, xoff_r, xcode, peq_f, peq_r, carry_f, carry_r, fv_f, fv_r, T, snap_f, snap_r;
   lcs::DBuf colsum, ent, ext, nch, entcnt, sel, chars;
   uint64_t host_word[1] = {0};
+  // stage events of the last profiled call: [0] start, [1] fill start, [2] fill end, [3] end
+  bool prof = false, prof_valid = false, prof_trace = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  uint64_t prof_blocks = 0, prof_cells = 0;
+  void mark(int k, cudaStream_t st) {
+    if (prof) cudaEventRecord(ev[k], st);
+  }
 
   uint16_t* codemap() { return (uint16_t*)((char*)small.p + lcs::kOffCodemap); }
   uint32_t* presence() { return (uint32_t*)((char*)small.p + lcs::kOffPresence); }

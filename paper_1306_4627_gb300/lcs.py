@@ -23,7 +23,8 @@ TRACEBACK = 1
 EXPORTS = (
     "lcs_strerror", "lcs_ctx_create", "lcs_ctx_destroy", "lcs_ctx_sync", "lcs_length", "lcs_length_dev",
     "lcs_traceback", "lcs_traceback_dev", "lcs_batch", "lcs_batch_dev", "lcs_serve_create", "lcs_serve_submit",
-    "lcs_serve_poll", "lcs_serve_wait", "lcs_result_release", "lcs_serve_destroy",
+    "lcs_serve_poll", "lcs_serve_wait", "lcs_result_release", "lcs_serve_destroy", "lcs_ctx_set_profiling",
+    "lcs_ctx_last_profile",
 )
 
 
@@ -36,6 +37,11 @@ class LCSError(RuntimeError):
 class ServeCfg(ctypes.Structure):
     _fields_ = [("max_queue", ctypes.c_uint32), ("max_batch", ctypes.c_uint32), ("hbm_budget_bytes", ctypes.c_uint64),
                 ("long_pair_cells_log2", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("prep_ms", ctypes.c_double), ("fill_ms", ctypes.c_double), ("trace_ms", ctypes.c_double),
+                ("total_ms", ctypes.c_double), ("fill_blocks", ctypes.c_uint64), ("cells", ctypes.c_uint64)]
 
 
 class Result(ctypes.Structure):
@@ -67,6 +73,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lcs_serve_wait": (ctypes.c_int, [vp, u64, ctypes.c_double, ctypes.POINTER(Result)]),
         "lcs_result_release": (None, [vp, u64]),
         "lcs_serve_destroy": (None, [vp]),
+        "lcs_ctx_set_profiling": (ctypes.c_int, [vp, ctypes.c_int]),
+        "lcs_ctx_last_profile": (ctypes.c_int, [vp, ctypes.POINTER(Profile)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -135,6 +143,14 @@ class Context:
 
     def sync(self) -> None:
         _check(_lib.lcs_ctx_sync(self._h), "lcs_ctx_sync")
+
+    def set_profiling(self, enable: bool = True) -> None:
+        _check(_lib.lcs_ctx_set_profiling(self._h, 1 if enable else 0), "lcs_ctx_set_profiling")
+
+    def last_profile(self) -> dict:
+        p = Profile()
+        _check(_lib.lcs_ctx_last_profile(self._h, ctypes.byref(p)), "lcs_ctx_last_profile")
+        return {k: getattr(p, k) for k, _ in Profile._fields_}
 
     # -- host buffers -------------------------------------------------------------------------------------------
     def length(self, x, y) -> int:

@@ -106,3 +106,45 @@ def test_capacity_error(ctx):
     with pytest.raises(lcs.LCSError) as e:
         ctx.traceback(b"ACGTACGT", b"ACGTTTTT", out_cap=2)
     assert e.value.code == lcs.ERR_CAPACITY
+
+
+# ---- full-size workloads ---------------------------------------------------------------------------------------
+
+@pytest.mark.slow
+@pytest.mark.parametrize("variant", ["uniform", "mutated"])
+def test_full_pair_65536_traceback(ctx, oracle, variant):
+    """m = n = 65536 DNA with traceback (1-bit bitmap of 537 MB), the single-pair benchmark size; exact vs oracle."""
+    if variant == "uniform":
+        x, y = gen.pair_uniform(65536, 65536, 4, seed=gen.BASE_SEED + 1)
+    else:
+        x, y = gen.pair_mutated(65536, 4, seed=gen.BASE_SEED + 1)
+    s = ctx.traceback(x, y)
+    assert s == oracle.lcs_traceback(x, y)
+    assert ctx.length(x, y) == len(s)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("sigma", [4, 20])
+def test_full_length_262144_properties(ctx, oracle, sigma):
+    """m = n = 262144, length only (multi-block wavefront, meet-in-the-middle). Properties that hold at any size:
+    the split length equals the forward-only length of the traceback path, and is symmetric and reversal
+    invariant; the traced string is a common subsequence of that length. Exact vs the oracle on a sub-problem
+    that spans all column blocks (the first 4096 rows of X against all of Y)."""
+    x, y = gen.pair_uniform(262144, 262144, sigma, seed=gen.BASE_SEED + 2)
+    L = ctx.length(x, y)
+    assert L == ctx.length(y, x)
+    assert L == ctx.length(x[::-1].copy(), y[::-1].copy())
+    s = ctx.traceback(x, y)
+    assert len(s) == L
+    assert oracle.is_subsequence(s, x.tobytes()) and oracle.is_subsequence(s, y.tobytes())
+    xs = x[:4096].copy()
+    assert ctx.length(xs, y) == oracle.lcs_length(xs, y)
+    assert ctx.traceback(xs, y) == oracle.lcs_traceback(xs, y)
+
+
+@pytest.mark.slow
+@pytest.mark.skipif(os.environ.get("LCS_FULL_ORACLE") != "1", reason="full 262144^2 oracle run takes minutes")
+@pytest.mark.parametrize("sigma", [4, 20])
+def test_full_length_262144_oracle(ctx, oracle, sigma):
+    x, y = gen.pair_uniform(262144, 262144, sigma, seed=gen.BASE_SEED + 2)
+    assert ctx.length(x, y) == oracle.lcs_length(x, y)
