@@ -1,6 +1,7 @@
 // C ABI of liblcs.so: contexts, LCS length and traceback for one pair (paper §I.C LCS-length, §I.D Print-LCS).
 // Host code only; the kernels live in lcs_prep.cu, lcs_fill.cu and lcs_trace.cu.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -75,6 +76,7 @@ int run_fill(lcs_ctx* c, FillJob* jobs, int njobs, bool traceback, cudaStream_t 
   FillArgs a{};
   a.status = c->status();
   a.spin_limit = c->spin_limit;
+  a.variant = c->fill_variant;
   uint32_t total = 0;
   for (int k = 0; k < njobs; ++k) total += jobs[k].nblocks_total;
   if (total <= (uint32_t)c->max_coop) {
@@ -84,7 +86,7 @@ int run_fill(lcs_ctx* c, FillJob* jobs, int njobs, bool traceback, cudaStream_t 
       a.job[k].nblocks = jobs[k].nblocks_total;
     }
     a.njobs = (uint32_t)njobs;
-    return from_cuda(launch_fill(a, 8, traceback, st));
+    return from_cuda(launch_fill(a, c->fill_B, traceback, st));
   }
   for (int k = 0; k < njobs; ++k) {
     for (uint32_t b0 = 0; b0 < jobs[k].nblocks_total; b0 += (uint32_t)c->max_coop) {
@@ -92,7 +94,7 @@ int run_fill(lcs_ctx* c, FillJob* jobs, int njobs, bool traceback, cudaStream_t 
       a.job[0].block0 = b0;
       a.job[0].nblocks = std::min<uint32_t>((uint32_t)c->max_coop, jobs[k].nblocks_total - b0);
       a.njobs = 1;
-      int rc = from_cuda(launch_fill(a, 8, traceback, st));
+      int rc = from_cuda(launch_fill(a, c->fill_B, traceback, st));
       if (rc) return rc;
     }
   }
@@ -125,7 +127,7 @@ static int prep_y(lcs_ctx* c, const uint8_t* d_y, uint64_t n, const Geo& g, bool
 int run_length(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, uint64_t n, uint64_t* d_out,
                cudaStream_t st) {
   if (m == 0 || n == 0) return from_cuda(cudaMemsetAsync(d_out, 0, sizeof(uint64_t), st));
-  const uint32_t B = 8;
+  const uint32_t B = c->fill_B;
   const Geo g = geo_for(n);
   // Meet in the middle: the top half of the rows forward, the bottom half on the reversed strings, at the same
   // time; L = max_j (c[mt, j] + LCS(X[mt+1..m], Y[j+1..n])) (the recurrence read from both ends).
@@ -138,10 +140,10 @@ int run_length(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, u
   c->mark(0, st);
   int rc = prep_y(c, d_y, n, g, split, st);
   if (rc) return rc;
-  rc = from_cuda(ensure(c->xoff_f, (Rf + 2 * kPadRowblocks) * B * 4));
+  rc = from_cuda(ensure(c->xoff_f, (Rf + kPadRowblocks + kPadBackRowblocks) * B * 4));
   if (!rc) rc = from_cuda(ensure(c->carry_f, g.nblocks * Rf * 4));
   if (!rc) rc = from_cuda(ensure(c->fv_f, g.wpad * 4));
-  if (!rc && split) rc = from_cuda(ensure(c->xoff_r, (Rr + 2 * kPadRowblocks) * B * 4));
+  if (!rc && split) rc = from_cuda(ensure(c->xoff_r, (Rr + kPadRowblocks + kPadBackRowblocks) * B * 4));
   if (!rc && split) rc = from_cuda(ensure(c->carry_r, g.nblocks * Rr * 4));
   if (!rc && split) rc = from_cuda(ensure(c->fv_r, g.wpad * 4));
   if (!rc && split) rc = from_cuda(ensure(c->colsum, (2 * (g.wq + 1) + 4) * 4));
@@ -193,11 +195,12 @@ int run_length(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, u
 int run_traceback(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, uint64_t n, uint8_t* d_out,
                   uint64_t out_cap, uint64_t* d_out_len, cudaStream_t st) {
   if (m == 0 || n == 0) return from_cuda(cudaMemsetAsync(d_out_len, 0, sizeof(uint64_t), st));
-  const uint32_t B = 8;
+  const uint32_t B = c->fill_B;
   const Geo g = geo_for(n);
-  // Segments of H rows (a multiple of B) for the parallel walk; at most kMaxSegments of them.
-  uint64_t H = (m + kMaxSegments - 1) / kMaxSegments;
-  H = std::max<uint64_t>(B, (H + B - 1) / B * B);
+  // Segments of H rows for the parallel walk, at most kMaxSegments of them. H is a multiple of 32 * B: the fill
+  // kernel snapshots a lane's word once per 32 steps.
+  const uint64_t unit = 32ull * B;
+  const uint64_t H = unit * ((m + kMaxSegments * unit - 1) / (kMaxSegments * unit));
   const uint64_t S = (m + H - 1) / H;
   const bool rev = S > 1;
   const uint64_t Rf = (m + B - 1) / B;
@@ -209,11 +212,11 @@ int run_traceback(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y
   int rc = prep_y(c, d_y, n, g, rev, st);
   if (rc) return rc;
   rc = from_cuda(ensure(c->T, t_bytes));
-  if (!rc) rc = from_cuda(ensure(c->xoff_f, (Rf + 2 * kPadRowblocks) * B * 4));
+  if (!rc) rc = from_cuda(ensure(c->xoff_f, (Rf + kPadRowblocks + kPadBackRowblocks) * B * 4));
   if (!rc) rc = from_cuda(ensure(c->xcode, m));
   if (!rc) rc = from_cuda(ensure(c->carry_f, g.nblocks * Rf * 4));
   if (!rc) rc = from_cuda(ensure(c->snap_f, S * g.wpad * 4));
-  if (!rc && rev) rc = from_cuda(ensure(c->xoff_r, (Rr + 2 * kPadRowblocks) * B * 4));
+  if (!rc && rev) rc = from_cuda(ensure(c->xoff_r, (Rr + kPadRowblocks + kPadBackRowblocks) * B * 4));
   if (!rc && rev) rc = from_cuda(ensure(c->carry_r, g.nblocks * Rr * 4));
   if (!rc && rev) rc = from_cuda(ensure(c->snap_r, S * g.wpad * 4));
   if (!rc) rc = from_cuda(ensure(c->colsum, (S * 2 * (g.wq + 1) + 4) * 4));
@@ -322,6 +325,8 @@ extern "C" int lcs_ctx_create(int device, lcs_ctx** out) {
     lcs_ctx_destroy(c);
     return rc;
   }
+  if (const char* e = getenv("LCS_FILL_B")) c->fill_B = (atoi(e) == 16) ? 16u : 8u;
+  if (const char* e = getenv("LCS_FILL_VARIANT")) c->fill_variant = (uint32_t)atoi(e);
   *out = c;
   return LCS_OK;
 }

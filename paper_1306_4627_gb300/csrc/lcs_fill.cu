@@ -33,59 +33,347 @@ __device__ __forceinline__ uint32_t ld_relaxed_gpu(const uint32_t* p) {
   asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ void st_relaxed_gpu(uint32_t* p, uint32_t v) {
-  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+// Predicated relaxed store (no branch around it): stores only when pred != 0.
+__device__ __forceinline__ void st_relaxed_gpu_if(uint32_t* p, uint32_t v, uint32_t pred) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.relaxed.gpu.global.u32 [%0], %1;\n\t}" ::"l"(p), "r"(v),
+      "r"(pred)
+      : "memory");
 }
-__device__ __forceinline__ uint32_t ld_vol_shared(const uint32_t* p) { return *(const volatile uint32_t*)p; }
-__device__ __forceinline__ void st_vol_shared(uint32_t* p, uint32_t v) { *(volatile uint32_t*)p = v; }
+__device__ __forceinline__ uint32_t lds_u32(uint32_t saddr) {
+  uint32_t v;
+  asm("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(saddr));
+  return v;
+}
+__device__ __forceinline__ uint32_t lds_vol_u32(uint32_t saddr) {
+  uint32_t v;
+  asm volatile("ld.volatile.shared.u32 %0, [%1];" : "=r"(v) : "r"(saddr) : "memory");
+  return v;
+}
+__device__ __forceinline__ void sts_vol_u32(uint32_t saddr, uint32_t v) {
+  asm volatile("st.volatile.shared.u32 [%0], %1;" ::"r"(saddr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void sts_vol_u32_if(uint32_t saddr, uint32_t v, uint32_t pred) {
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.volatile.shared.u32 [%0], %1;\n\t}" ::"r"(saddr),
+               "r"(v), "r"(pred)
+               : "memory");
+}
 
-// Slot = carry bits (the top B bits, row 0 of the block at bit 31) | tag (low 32-B bits, never 0).
+// Bounded waits. A wait that gives up (its own timeout, or the abort flag raised after another warp's timeout)
+// records the timeout in the status word; the warp then stops waiting for the rest of the launch.
+__device__ __forceinline__ bool give_up(DevStatus* st, uint32_t it, uint32_t limit, uint32_t where) {
+  if (*(volatile uint32_t*)&st->abort) return true;
+  if (it >= limit) {
+    atomicOr(&st->flags, kStatTimeout);
+    atomicExch(&st->where, where);
+    atomicExch(&st->abort, 1u);
+    return true;
+  }
+  return false;
+}
+
+// Waits (all lanes together) for a tagged slot: global (relaxed, gpu scope) or shared (volatile).
+// Returns (gave_up << 32) | value.
+__device__ __noinline__ uint64_t spin_slot(const uint32_t* gp, uint32_t saddr, bool global, uint32_t want,
+                                           uint32_t tmask, DevStatus* st, uint32_t limit) {
+  for (uint32_t it = 0;; ++it) {
+    const uint32_t v = global ? ld_relaxed_gpu(gp) : lds_vol_u32(saddr);
+    if ((v & tmask) == want) return v;
+    if ((it & 63u) == 63u && give_up(st, it, limit, global ? 1u : 2u)) return (1ull << 32) | v;
+    __nanosleep(32);
+  }
+}
+
+// Waits (all lanes together) until the consumer of a shared-memory ring has consumed row-blocks below `need`.
+__device__ __noinline__ bool spin_ring_space(uint32_t cons_saddr, uint32_t need, DevStatus* st, uint32_t limit) {
+  for (uint32_t it = 0;; ++it) {
+    const uint32_t c = lds_vol_u32(cons_saddr);
+    if ((int32_t)(c - need) >= 0) return true;
+    if ((it & 63u) == 63u && give_up(st, it, limit, 3u)) return false;
+    __nanosleep(32);
+  }
+}
+
 template <int B>
-__device__ __forceinline__ uint32_t slot_tag(uint64_t r) {
-  constexpr uint32_t mask = (1u << (32 - B)) - 1u;
-  return ((uint32_t)(r + 1) | 1u) & mask;
-}
-
-__device__ __noinline__ uint32_t spin_slot(const uint32_t* p, bool global, uint32_t want, uint32_t tmask,
-                                           DevStatus* st, uint32_t limit, bool& failed, uint32_t where) {
-  uint32_t v = 0;
-  for (uint32_t it = 0;; ++it) {
-    v = global ? ld_relaxed_gpu(p) : ld_vol_shared(p);
-    if ((v & tmask) == want || failed) return v;
-    if ((it & 127u) == 127u) {
-      if (*(volatile uint32_t*)&st->abort) { failed = true; return v; }
-      if (it >= limit) {
-        atomicOr(&st->flags, kStatTimeout);
-        atomicExch(&st->where, where);
-        atomicExch(&st->abort, 1u);
-        failed = true;
-        return v;
-      }
-    }
-    __nanosleep(64);
+__device__ __forceinline__ void load_xo(const uint4* p, uint32_t (&dst)[B]) {
+#pragma unroll
+  for (int v = 0; v < B / 4; ++v) {
+    const uint4 q4 = __ldg(p + v);
+    dst[4 * v + 0] = q4.x;
+    dst[4 * v + 1] = q4.y;
+    dst[4 * v + 2] = q4.z;
+    dst[4 * v + 3] = q4.w;
   }
 }
 
-__device__ __noinline__ void spin_ring_space(const uint32_t* cons, uint64_t r, DevStatus* st, uint32_t limit,
-                                             bool& failed) {
-  for (uint32_t it = 0;; ++it) {
-    const uint32_t c = ld_vol_shared(cons);
-    if ((int64_t)r - (int64_t)c < (int64_t)(kRing - 64) || failed) return;
-    if ((it & 127u) == 127u) {
-      if (*(volatile uint32_t*)&st->abort) { failed = true; return; }
-      if (it >= limit) {
-        atomicOr(&st->flags, kStatTimeout);
-        atomicExch(&st->where, 3u);
-        atomicExch(&st->abort, 1u);
-        failed = true;
-        return;
+// Where a warp's inbound carries come from and where its outbound carries go.
+enum : int { kSrcNone = 0, kSrcGlobal = 1, kSrcRing = 2 };
+enum : int { kDstNone = 0, kDstGlobal = 1, kDstRing = 2 };
+
+// Constants of one warp.
+struct Warp {
+  uint32_t peq_lane;   // shared-memory address of this lane's column of the match masks
+  uint32_t ring_src;   // shared-memory ring read by lane 0 (row-block r at slot r % kRing)
+  uint32_t ring_dst;   // shared-memory ring written by lane 31
+  uint32_t cons_self;  // this warp's consumption counter (read by the producer for back-pressure)
+  uint32_t cons_next;  // the next warp's consumption counter
+  uint32_t xring;     // shared-memory ring of symbol offsets: row-block rb at slot rb % 64 (B words each)
+  const uint32_t* xoff;  // global symbol offsets: row-block rb at xoff + (rb + kPadRowblocks) * B
+  const uint32_t* src_g;
+  uint32_t* dst_g;
+  DevStatus* status;
+  uint32_t* snap;     // snapshot rows [k][wpad] (k = (r + 1) / snap_rb - 1), this lane's column
+  uint64_t wpad;
+  int32_t R;
+  uint32_t lane, snap_rb, spin_limit;
+  uint32_t cap_k;     // step (mod 32) at which this lane finishes a row-block r with (r + 1) % 32 == 0
+};
+
+// Loop state of one lane, kept in registers across the unrolled steps.
+struct Lane {
+  uint32_t V;         // the lane's word of the current row vector
+  uint32_t cout;      // carry bits produced in the last step (row 0 of the block at bit 31)
+  uint32_t win_cur;   // inbound global window: slot 32*floor(t/32) + lane
+  uint32_t win_next;  // the following 32 slots
+  uint32_t q0, q1;    // inbound ring slots requested two steps ahead (even / odd steps)
+  uint32_t cap;       // V captured at the end of this lane's row-block r with (r + 1) % 32 == 0 in this block
+  uint32_t xstage[16];  // symbol offsets of row-block t0 + 33 + lane, staged for the next 32-step boundary
+  uint4* tp;          // this step's bitmap chunk of the warp, plus this lane's offset
+  bool failed;
+};
+
+// The B rows of one step. KT selects the row form: 0 = U = V & P; S = V + U + c; V' = S | (V & ~P) (three
+// dependent operations per row); 1 = the same values with V & ~P carried from the previous row, so that V' and
+// the next row's U come from S in one operation each (two dependent operations per row).
+template <int B, bool TB, int KT>
+__device__ __forceinline__ void rows(uint32_t peq_lane, const uint32_t (&xo)[B], uint32_t& V, uint32_t cin,
+                                     uint32_t& co, uint32_t (&tw)[B]) {
+  uint32_t cw = cin;
+  co = 0;
+  if (KT == 0) {
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const uint32_t P = lds_u32(peq_lane + xo[b]);
+      const uint32_t U = V & P;
+      uint32_t S;
+      asm("add.cc.u32 %0, %0, %0;\n\t"
+          "addc.cc.u32 %1, %3, %4;\n\t"
+          "addc.u32 %2, %2, %2;"
+          : "+r"(cw), "=r"(S), "+r"(co)
+          : "r"(V), "r"(U));
+      if (TB) tw[b] = S ^ V ^ U;
+      V = S | (V & ~P);
+    }
+  } else {
+    uint32_t P[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) P[b] = lds_u32(peq_lane + xo[b]);
+    uint32_t U = V & P[0], N = V & ~P[0];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      uint32_t S;
+      asm("add.cc.u32 %0, %0, %0;\n\t"
+          "addc.cc.u32 %1, %3, %4;\n\t"
+          "addc.u32 %2, %2, %2;"
+          : "+r"(cw), "=r"(S), "+r"(co)
+          : "r"(V), "r"(U));
+      if (TB) tw[b] = S ^ V ^ U;
+      if (b + 1 < B) {
+        // V' = S | N, U' = (S | N) & P', N' = (S | N) & ~P', each one LOP3 straight from S
+        const uint32_t Pn = P[b + 1 < B ? b + 1 : b];
+        uint32_t Un, Nn;
+        asm("lop3.b32 %0, %1, %2, %3, 0xA8;" : "=r"(Un) : "r"(S), "r"(N), "r"(Pn));
+        asm("lop3.b32 %0, %1, %2, %3, 0x54;" : "=r"(Nn) : "r"(S), "r"(N), "r"(Pn));
+        V = S | N;
+        U = Un;
+        N = Nn;
+      } else {
+        V = S | N;
       }
     }
-    __nanosleep(64);
   }
 }
 
-template <int B, bool TB>
+// One step of one warp: lane l updates its word over the B rows of row-block r = t - l. Every load of the step
+// was issued at least one step earlier; the only lane-dependent work (lane 0 taking the previous warp's carries,
+// lane 31 handing its carries on, snapshots) is predicated, so the warp never diverges in the common case.
+template <int B, bool TB, int KT, bool SNAP, int SRC, int DST, int PAR>
+__device__ __forceinline__ void fill_step(const Warp& w, Lane& s, int32_t t, const uint32_t (&xo)[B],
+                                          uint32_t (&xn)[B]) {
+  constexpr uint32_t kTagMask = (1u << (32 - B)) - 1u;
+  const uint32_t lane = w.lane;
+  const int32_t r = t - (int32_t)lane;
+  {  // symbol offsets of the next step's row-block (t + 1 - lane) from the warp's shared ring
+    const uint32_t a = w.xring + (((uint32_t)(r + 1)) & 63u) * (B * 4);
+#pragma unroll
+    for (int v = 0; v < B / 4; ++v) {
+      uint32_t q0, q1, q2, q3;
+      asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(q0), "=r"(q1), "=r"(q2), "=r"(q3) : "r"(a + 16 * v));
+      xn[4 * v] = q0;
+      xn[4 * v + 1] = q1;
+      xn[4 * v + 2] = q2;
+      xn[4 * v + 3] = q3;
+    }
+  }
+  const uint32_t c_up = __shfl_up_sync(kFull, s.cout, 1);
+  uint32_t cin0 = 0;
+  if (SRC != kSrcNone) {
+    uint32_t src;  // the same value in every lane
+    if (SRC == kSrcGlobal) {
+      src = __shfl_sync(kFull, s.win_cur, t & 31);
+    } else {
+      src = PAR ? s.q1 : s.q0;
+      const uint32_t nq = lds_vol_u32(w.ring_src + (((uint32_t)t + 2u) & (kRing - 1)) * 4u);
+      if (PAR) s.q1 = nq; else s.q0 = nq;
+    }
+    const uint32_t want = ((uint32_t)(t + 1) | 1u) & kTagMask;
+    if (t < w.R && (src & kTagMask) != want && !s.failed) {  // warp-uniform, rare after the first steps
+      const uint64_t res = spin_slot(w.src_g + t, w.ring_src + ((uint32_t)t & (kRing - 1)) * 4u,
+                                     SRC == kSrcGlobal, want, kTagMask, w.status, w.spin_limit);
+      src = (uint32_t)res;
+      s.failed = (res >> 32) != 0;
+    }
+    cin0 = t < w.R ? (src & ~kTagMask) : 0u;
+  }
+  const uint32_t cin = lane == 0 ? cin0 : c_up;
+  uint32_t co, V = s.V;
+  uint32_t tw[B];
+  rows<B, TB, KT>(w.peq_lane, xo, V, cin, co, tw);
+  s.V = V;
+  s.cout = co << (32 - B);
+  if (TB) {
+#pragma unroll
+    for (int v = 0; v < B / 4; ++v) s.tp[v * 32] = make_uint4(tw[4 * v], tw[4 * v + 1], tw[4 * v + 2], tw[4 * v + 3]);
+    s.tp += 8 * B;  // 32 lanes x B words = 8 * B uint4 per step
+  }
+  if (SNAP) s.cap = (((uint32_t)t & 31u) == w.cap_k) ? V : s.cap;
+  if (DST != kDstNone) {  // lane 31 hands its carries for row-block t - 31 to the next warp
+    const uint32_t r31 = (uint32_t)(t - 31);
+    const uint32_t v = s.cout | ((r31 + 1u) | 1u) & kTagMask;
+    const uint32_t pred = (lane == 31) & (t >= 31);
+    if (DST == kDstGlobal) st_relaxed_gpu_if(w.dst_g + (int64_t)t - 31, v, pred);
+    else sts_vol_u32_if(w.ring_dst + (r31 & (kRing - 1)) * 4u, v, pred);
+  }
+}
+
+// Loads the symbol offsets of row-block rb (B words) from global memory into registers.
+template <int B>
+__device__ __forceinline__ void xo_load_global(const Warp& w, int32_t rb, uint32_t* dst) {
+  const uint4* p = reinterpret_cast<const uint4*>(w.xoff + (int64_t)(rb + kPadRowblocks) * B);
+#pragma unroll
+  for (int v = 0; v < B / 4; ++v) {
+    const uint4 q = __ldg(p + v);
+    dst[4 * v] = q.x;
+    dst[4 * v + 1] = q.y;
+    dst[4 * v + 2] = q.z;
+    dst[4 * v + 3] = q.w;
+  }
+}
+template <int B>
+__device__ __forceinline__ void xo_store_ring(const Warp& w, int32_t rb, const uint32_t* src) {
+  const uint32_t a = w.xring + ((uint32_t)rb & 63u) * (B * 4);
+#pragma unroll
+  for (int v = 0; v < B / 4; ++v)
+    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(a + 16 * v), "r"(src[4 * v]), "r"(src[4 * v + 1]),
+                 "r"(src[4 * v + 2]), "r"(src[4 * v + 3])
+                 : "memory");
+}
+
+// Refill of the symbol-offset ring at a 32-step boundary t0: during steps t0 .. t0+31 the lanes read row-blocks
+// t0-30 .. t0+32; the ring (64 row-blocks) then holds t0-31 .. t0+32. The row-blocks t0+1 .. t0+32 were loaded
+// into registers at the previous boundary; the next ones are requested now and stored 32 steps later.
+template <int B>
+__device__ __forceinline__ void xo_refill(const Warp& w, Lane& s, int32_t t0) {
+  __syncwarp();
+  xo_store_ring<B>(w, t0 + 1 + (int32_t)w.lane, s.xstage);
+  __syncwarp();
+  xo_load_global<B>(w, t0 + 33 + (int32_t)w.lane, s.xstage);
+}
+
+// After the 32-step block starting at t0 (or the shorter last block ending at `end`): store the captured V when its
+// row-block r = t0 + cap_k - lane is one whose end row is snapshotted, (r + 1) % snap_rb == 0.
+__device__ __forceinline__ void snap_store(const Warp& w, const Lane& s, int32_t t0, int32_t end) {
+  const int32_t r = t0 + (int32_t)w.cap_k - (int32_t)w.lane;
+  if (t0 + (int32_t)w.cap_k < end && r >= 0 && r < w.R && ((uint32_t)(r + 1) % w.snap_rb) == 0)
+    w.snap[(uint64_t)((uint32_t)(r + 1) / w.snap_rb - 1) * w.wpad] = s.cap;
+}
+
+// Work at the start of each 32-step block: publish consumption, honour ring back-pressure.
+template <int SRC, int DST>
+__device__ __forceinline__ void block_start(const Warp& w, Lane& s, int32_t t) {
+  if (SRC == kSrcRing) sts_vol_u32(w.cons_self, (uint32_t)t);  // all lanes write the same value
+  if (DST == kDstRing && !s.failed) {
+    // this block writes row-blocks up to t; they overwrite slot r - kRing, which must be consumed
+    const uint32_t need = (uint32_t)(t - (kRing - 64));
+    if (t >= kRing - 64 && (int32_t)(lds_vol_u32(w.cons_next) - need) < 0)
+      s.failed = !spin_ring_space(w.cons_next, need, w.status, w.spin_limit);
+  }
+}
+
+template <int B, bool TB, int KT, bool SNAP, int SRC, int DST>
+__device__ __forceinline__ void warp_loop(const Warp& w, Lane& s) {
+  uint32_t xa[B], xb[B];
+  {  // ring: row-blocks -31 .. 0 now, 1 .. 32 at the first boundary (t0 = 0), 33 .. 64 staged
+    uint32_t tmp[B];
+    xo_load_global<B>(w, -31 + (int32_t)w.lane, tmp);
+    xo_store_ring<B>(w, -31 + (int32_t)w.lane, tmp);
+    xo_load_global<B>(w, 1 + (int32_t)w.lane, s.xstage);
+    __syncwarp();
+    const uint32_t a = w.xring + ((uint32_t)(-(int32_t)w.lane) & 63u) * (B * 4);  // row-block -lane, step 0
+#pragma unroll
+    for (int v = 0; v < B / 4; ++v) {
+      uint32_t q0, q1, q2, q3;
+      asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(q0), "=r"(q1), "=r"(q2), "=r"(q3) : "r"(a + 16 * v));
+      xa[4 * v] = q0;
+      xa[4 * v + 1] = q1;
+      xa[4 * v + 2] = q2;
+      xa[4 * v + 3] = q3;
+    }
+    xo_refill<B>(w, s, 0);
+  }
+  const int32_t steps = w.R + 31;
+  int32_t t = 0;
+  for (; t + 32 <= steps; t += 32) {
+    if (t) xo_refill<B>(w, s, t);
+    block_start<SRC, DST>(w, s, t);
+#pragma unroll 1
+    for (int k = 0; k < 16; k += 2) {
+      fill_step<B, TB, KT, SNAP, SRC, DST, 0>(w, s, t + k, xa, xb);
+      fill_step<B, TB, KT, SNAP, SRC, DST, 1>(w, s, t + k + 1, xb, xa);
+    }
+    if (SRC == kSrcGlobal) {  // the next window, 16 steps before it is needed
+      const int32_t q = t + 32 + (int32_t)w.lane;
+      s.win_next = q < w.R ? ld_relaxed_gpu(w.src_g + q) : 0u;
+    }
+#pragma unroll 1
+    for (int k = 16; k < 32; k += 2) {
+      fill_step<B, TB, KT, SNAP, SRC, DST, 0>(w, s, t + k, xa, xb);
+      fill_step<B, TB, KT, SNAP, SRC, DST, 1>(w, s, t + k + 1, xb, xa);
+    }
+    if (SRC == kSrcGlobal) s.win_cur = s.win_next;
+    if (SNAP) snap_store(w, s, t, steps);
+  }
+  if (t) xo_refill<B>(w, s, t);
+  block_start<SRC, DST>(w, s, t);
+  const int32_t t_tail = t;
+  for (; t + 1 < steps; t += 2) {
+    fill_step<B, TB, KT, SNAP, SRC, DST, 0>(w, s, t, xa, xb);
+    fill_step<B, TB, KT, SNAP, SRC, DST, 1>(w, s, t + 1, xb, xa);
+  }
+  if (t < steps) fill_step<B, TB, KT, SNAP, SRC, DST, 0>(w, s, t, xa, xb);
+  if (SNAP) snap_store(w, s, t_tail, steps);
+}
+
+template <int B, bool TB, int KT, bool SNAP>
+__device__ __forceinline__ void dispatch(const Warp& w, Lane& s, bool first_warp, bool last_warp, uint32_t wib) {
+  if (first_warp) warp_loop<B, TB, KT, SNAP, kSrcNone, kDstRing>(w, s);
+  else if (wib == 0) warp_loop<B, TB, KT, SNAP, kSrcGlobal, kDstRing>(w, s);
+  else if (wib + 1 < kFillWarps) warp_loop<B, TB, KT, SNAP, kSrcRing, kDstRing>(w, s);
+  else if (!last_warp) warp_loop<B, TB, KT, SNAP, kSrcRing, kDstGlobal>(w, s);
+  else warp_loop<B, TB, KT, SNAP, kSrcRing, kDstNone>(w, s);
+}
+
+template <int B, bool TB, int KT>
 __global__ void __launch_bounds__(kFillThreads, 1) k_fill(const __grid_constant__ FillArgs a) {
   static_assert(B % 4 == 0 && B >= 4 && B <= 16, "row-block height");
   extern __shared__ __align__(16) uint32_t sm[];
@@ -100,9 +388,10 @@ __global__ void __launch_bounds__(kFillThreads, 1) k_fill(const __grid_constant_
   const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const uint32_t sigr = *J.sigma_rows;
 
-  uint32_t* ring = sm;                       // [kFillWarps-1][kRing]: ring w carries warp w -> warp w+1
-  uint32_t* cons = sm + (kFillWarps - 1) * kRing;  // [kFillWarps] consumer progress (row-blocks consumed)
-  uint32_t* peq_s = cons + 8;                // [sigr][kStripeWords], this block's stripe of the match masks
+  uint32_t* ring = sm;                             // [kFillWarps-1][kRing]: ring w carries warp w -> warp w+1
+  uint32_t* cons = sm + (kFillWarps - 1) * kRing;  // [kFillWarps] consumption counters
+  uint32_t* xring = cons + 8;                      // [kFillWarps][64][B] symbol-offset rings
+  uint32_t* peq_s = xring + kFillWarps * 64 * 16;  // [sigr][kStripeWords]: this block's stripe of the masks
   for (uint32_t i = threadIdx.x; i < (kFillWarps - 1) * kRing + 8; i += kFillThreads) sm[i] = 0;
   const uint64_t col0 = (uint64_t)blk * kStripeWords;
   for (uint32_t i = threadIdx.x; i < sigr * kStripeWords; i += kFillThreads) {
@@ -111,116 +400,57 @@ __global__ void __launch_bounds__(kFillThreads, 1) k_fill(const __grid_constant_
   }
   __syncthreads();
 
-  const uint64_t R = J.R;
   const uint64_t gw = (uint64_t)blk * kFillWarps + wib;
   const bool first_warp = (gw == 0);
-  const bool src_global = (wib == 0);
-  const bool dst_global = (wib == kFillWarps - 1);
-  const bool has_consumer = !(dst_global && blk + 1 >= J.nblocks_total);
-  const uint32_t* src_g = (src_global && !first_warp) ? J.carry + (uint64_t)(blk - 1) * R : nullptr;
-  const uint32_t* src_s = ring + (wib == 0 ? 0 : (wib - 1)) * kRing;
-  uint32_t* dst_g = J.carry + (uint64_t)blk * R;
-  uint32_t* dst_s = ring + (dst_global ? 0 : wib) * kRing;
-  const char* peq_lane = reinterpret_cast<const char*>(peq_s) + (wib * 32 + lane) * 4;
-  constexpr uint32_t kTagMask = (1u << (32 - B)) - 1u;
-  bool failed = false;
+  const bool last_warp = (wib == kFillWarps - 1) && (blk + 1 >= J.nblocks_total);
+  Warp w;
+  w.lane = lane;
+  w.R = (int32_t)J.R;
+  w.wpad = J.wpad;
+  w.snap_rb = J.snap_rb;
+  w.spin_limit = a.spin_limit;
+  w.status = a.status;
+  w.src_g = (wib == 0 && !first_warp) ? J.carry + (uint64_t)(blk - 1) * J.R : J.carry;
+  w.dst_g = J.carry + (uint64_t)blk * J.R;
+  w.peq_lane = (uint32_t)__cvta_generic_to_shared(peq_s) + (wib * 32 + lane) * 4u;
+  w.xring = (uint32_t)__cvta_generic_to_shared(xring + wib * 64 * B);
+  w.xoff = J.xoff;
+  w.ring_src = (uint32_t)__cvta_generic_to_shared(ring + (wib == 0 ? 0 : wib - 1) * kRing);
+  w.ring_dst = (uint32_t)__cvta_generic_to_shared(ring + (wib + 1 < kFillWarps ? wib : 0) * kRing);
+  w.cons_self = (uint32_t)__cvta_generic_to_shared(cons + wib);
+  w.cons_next = (uint32_t)__cvta_generic_to_shared(cons + (wib + 1 < kFillWarps ? wib + 1 : wib));
 
-  auto load_slot = [&](uint64_t s) -> uint32_t {
-    if (first_warp || s >= R) return 0u;
-    return src_global ? ld_relaxed_gpu(src_g + s) : ld_vol_shared(src_s + (s % kRing));
-  };
-  uint32_t win_cur = load_slot(lane), win_next = load_slot(32 + lane);
+  Lane s;
+  s.V = kFull;
+  s.cout = 0;
+  s.failed = false;
+  s.cap = 0;
+  w.snap = J.snap ? J.snap + gw * 32 + lane : nullptr;
+  w.cap_k = (lane + 31u) & 31u;
+  s.win_cur = (wib == 0 && !first_warp && (int32_t)lane < w.R) ? ld_relaxed_gpu(w.src_g + lane) : 0u;
+  s.win_next = 0;
+  s.q0 = 0;
+  s.q1 = 0;
+  s.tp = J.T ? reinterpret_cast<uint4*>(J.T + (gw * (J.R + 31)) * 32 * (uint64_t)B) + lane : nullptr;
 
-  uint64_t next_snap = J.snap_rb ? (uint64_t)J.snap_rb - 1 : ~0ull;  // next row-block whose end is snapshotted
-  uint32_t* snap_lane = J.snap ? J.snap + gw * 32 + lane : nullptr;
-  uint64_t snap_idx = 0;
-  uint32_t V = kFull;
-  uint32_t cout_prev = 0;
-  const uint64_t steps = R + 31;
-  for (uint64_t t = 0; t < steps; ++t) {
-    const int64_t r = (int64_t)t - (int64_t)lane;
-    // symbol offsets of the B rows of this lane's row-block (the array has zero rows around [0, R))
-    const uint4* xo4 = reinterpret_cast<const uint4*>(J.xoff + (uint64_t)(r + kPadRowblocks) * B);
-    uint32_t xo[B];
-#pragma unroll
-    for (int v = 0; v < B / 4; ++v) {
-      const uint4 q4 = __ldg(xo4 + v);
-      xo[4 * v + 0] = q4.x;
-      xo[4 * v + 1] = q4.y;
-      xo[4 * v + 2] = q4.z;
-      xo[4 * v + 3] = q4.w;
-    }
-    // carries entering this lane's word: from lane-1's previous step; lane 0 from the previous warp
-    uint32_t cin = __shfl_up_sync(kFull, cout_prev, 1);
-    const uint32_t wv = __shfl_sync(kFull, win_cur, (int)(t & 31));
-    if (lane == 0) {
-      cin = 0;
-      if (!first_warp && t < R) {
-        uint32_t v = wv;
-        if ((v & kTagMask) != slot_tag<B>(t)) {
-          const uint32_t* p = src_global ? (src_g + t) : (src_s + (t % kRing));
-          v = spin_slot(p, src_global, slot_tag<B>(t), kTagMask, a.status, a.spin_limit, failed,
-                        src_global ? 1u : 2u);
-        }
-        cin = v & ~kTagMask;
-      }
-      if (!src_global && (t & 31) == 0) st_vol_shared(&cons[wib], (uint32_t)t);
-    }
-    if ((t & 31) == 31) {
-      win_cur = win_next;
-      win_next = load_slot(t + 33 + lane);
-    }
-    // B rows of the bit-parallel update; the carry bits enter at the MSB of cw and leave into the LSB of co
-    uint32_t cw = cin, co = 0;
-    uint32_t tw[B];
-#pragma unroll
-    for (int b = 0; b < B; ++b) {
-      const uint32_t P = *reinterpret_cast<const uint32_t*>(peq_lane + xo[b]);
-      const uint32_t U = V & P;
-      uint32_t S;
-      asm("add.cc.u32 %0, %0, %0;\n\t"
-          "addc.cc.u32 %1, %3, %4;\n\t"
-          "addc.u32 %2, %2, %2;"
-          : "+r"(cw), "=r"(S), "+r"(co)
-          : "r"(V), "r"(U));
-      if (TB) tw[b] = S ^ V ^ U;
-      V = S | (V & ~P);
-    }
-    cout_prev = co << (32 - B);
-    if (TB && J.T) {
-      uint4* chunk = reinterpret_cast<uint4*>(J.T + ((gw * (R + 31) + t) * 32) * (uint64_t)B);
-#pragma unroll
-      for (int v = 0; v < B / 4; ++v)
-        chunk[v * 32 + lane] = make_uint4(tw[4 * v], tw[4 * v + 1], tw[4 * v + 2], tw[4 * v + 3]);
-    }
-    if (snap_lane && r == (int64_t)next_snap) {
-      if ((uint64_t)r < R) snap_lane[snap_idx * J.wpad] = V;
-      next_snap += J.snap_rb;
-      ++snap_idx;
-    }
-    if (lane == 31 && has_consumer) {
-      const int64_t r31 = (int64_t)t - 31;
-      if (r31 >= 0 && (uint64_t)r31 < R) {
-        const uint32_t v = cout_prev | slot_tag<B>((uint64_t)r31);
-        if (dst_global) {
-          st_relaxed_gpu(dst_g + r31, v);
-        } else {
-          if ((r31 & 31) == 0) spin_ring_space(&cons[wib + 1], (uint64_t)r31, a.status, a.spin_limit, failed);
-          st_vol_shared(dst_s + ((uint64_t)r31 % kRing), v);
-        }
-      }
-    }
+  if (TB && J.T) {
+    dispatch<B, true, KT, true>(w, s, first_warp, last_warp, wib);
+  } else if (TB && J.snap) {  // the table of the reversed strings in a traceback launch: snapshots, no bitmap
+    dispatch<B, false, KT, true>(w, s, first_warp, last_warp, wib);
+  } else {
+    dispatch<B, false, KT, false>(w, s, first_warp, last_warp, wib);
   }
-  if (J.final_v) J.final_v[gw * 32 + lane] = V;
+
+  if (J.final_v) J.final_v[gw * 32 + lane] = s.V;
   if (J.len_acc) {
-    const uint32_t z = __reduce_add_sync(kFull, (uint32_t)__popc(~V));
+    const uint32_t z = __reduce_add_sync(kFull, (uint32_t)__popc(~s.V));
     if (lane == 0 && z) atomicAdd(J.len_acc, (unsigned long long)z);
   }
 }
 
-template <int B, bool TB>
+template <int B, bool TB, int KT>
 cudaError_t launch_t(const FillArgs& a, cudaStream_t st) {
-  auto fn = k_fill<B, TB>;
+  auto fn = k_fill<B, TB, KT>;
   const size_t smem = fill_smem_bytes();
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -232,22 +462,32 @@ cudaError_t launch_t(const FillArgs& a, cudaStream_t st) {
 }  // namespace
 
 size_t fill_smem_bytes() {
-  return ((size_t)(kFillWarps - 1) * kRing + 8 + (size_t)kSigmaMax * kStripeWords) * sizeof(uint32_t);
+  return ((size_t)(kFillWarps - 1) * kRing + 8 + (size_t)kFillWarps * 64 * 16 + (size_t)kSigmaMax * kStripeWords) *
+         sizeof(uint32_t);
 }
 
 int fill_max_coop_blocks(int device) {
   int sms = 0, per_sm = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
-  auto fn = k_fill<8, true>;
+  auto fn = k_fill<8, true, 0>;
   const size_t smem = fill_smem_bytes();
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kFillThreads, smem) != cudaSuccess) return 0;
   return sms * per_sm;
 }
 
+// variant: bit 0 = shorter row chain (KT); B = rows per step (8 or 16)
 cudaError_t launch_fill(const FillArgs& a, uint32_t B, bool traceback, cudaStream_t st) {
-  if (B != 8) return cudaErrorInvalidValue;
-  return traceback ? launch_t<8, true>(a, st) : launch_t<8, false>(a, st);
+  const int kt = (a.variant & 1) ? 1 : 0;
+  if (B == 8) {
+    if (traceback) return kt ? launch_t<8, true, 1>(a, st) : launch_t<8, true, 0>(a, st);
+    return kt ? launch_t<8, false, 1>(a, st) : launch_t<8, false, 0>(a, st);
+  }
+  if (B == 16) {
+    if (traceback) return kt ? launch_t<16, true, 1>(a, st) : launch_t<16, true, 0>(a, st);
+    return kt ? launch_t<16, false, 1>(a, st) : launch_t<16, false, 0>(a, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace lcs

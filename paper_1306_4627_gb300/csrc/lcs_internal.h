@@ -17,7 +17,8 @@ constexpr int kFillThreads = kFillWarps * 32;
 constexpr int kStripeWords = kFillThreads;
 constexpr int kRing = 256;              // slots of the shared-memory carry ring between neighbouring warps
 constexpr int kSigmaMax = 257;          // up to 256 byte values present in Y, plus the all-zero row
-constexpr int kPadRowblocks = 32;       // zero row-blocks in front of and behind every row-offset array
+constexpr int kPadRowblocks = 32;       // zero row-blocks in front of every row-offset array
+constexpr int kPadBackRowblocks = 128;  // zero row-blocks behind it (the fill reads up to 95 row-blocks past the end)
 
 // ---- device status word (latched errors) ---------------------------------------------------------------------
 constexpr uint32_t kStatTimeout = 1u;   // a bounded spin-wait expired
@@ -33,7 +34,7 @@ struct DevStatus {
 // One DP problem for the fill kernel (a forward table, or the table of the reversed strings).
 struct FillJob {
   const uint32_t* xoff;     // per padded row: byte offset of its symbol's row in the block's shared Peq stripe;
-                            // (kPadRowblocks + R + kPadRowblocks) * B entries
+                            // (kPadRowblocks + R + kPadBackRowblocks) * B entries
   const uint32_t* peq;      // match masks [sigma row][wpad], row 'sigma' (the last) all zero
   const uint32_t* sigma_rows;  // device word: rows of peq in use (present symbols + 1)
   uint32_t* carry;          // [nblocks_total][R] hand-off slots, block b's last warp -> block b+1's first warp
@@ -54,7 +55,7 @@ struct FillArgs {
   uint32_t njobs;
   DevStatus* status;
   uint32_t spin_limit;      // iterations of a bounded wait before it gives up
-  uint32_t pad;
+  uint32_t variant;         // bit 0: shorter dependent chain per row (same results)
 };
 
 // ---- traceback segment walkers ---------------------------------------------------------------------------------

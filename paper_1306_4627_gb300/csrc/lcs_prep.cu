@@ -90,7 +90,7 @@ cudaError_t launch_alphabet(const uint8_t* y, uint64_t n, uint32_t* presence8, u
 cudaError_t launch_xoff(const uint8_t* x, uint64_t m, bool reverse, uint64_t pad_front, uint64_t R, uint32_t B,
                         const uint16_t* codemap, const uint32_t* sigma_rows, uint32_t* xoff, uint8_t* xcode,
                         cudaStream_t st) {
-  const uint64_t total = (R + 2 * (uint64_t)kPadRowblocks) * B;
+  const uint64_t total = (R + (uint64_t)kPadRowblocks + kPadBackRowblocks) * B;
   k_xoff<<<grid_for(total, 256), 256, 0, st>>>(x, m, reverse ? 1 : 0, pad_front, total, B, codemap, sigma_rows,
                                                xoff, xcode);
   return cudaGetLastError();

@@ -109,10 +109,12 @@ __global__ void k_corr_cols(TraceArgs a) {
 // ---- the walk of one segment -------------------------------------------------------------------------------------
 // Direction bit of cell (i, c): bit c%32 of T-frame word c/32 of row i holds c[i,c] - c[i-1,c] (the carry into
 // column c+1's bit); 0 = UP, 1 = LEFT on a mismatch. Match bit of (i, c): bit (c-1)%32 of Peq word (c-1)/32.
+// Bitmap layout of the fill kernel: warp g's chunk for step t holds, for each of its 32 lanes, the B words of the
+// row-block that lane processed at that step (lane l at step t: row-block t - l), as [B/4][32 lanes][4 words].
 __device__ __forceinline__ uint32_t t_word(const TraceArgs& a, uint64_t i, uint64_t Q) {
-  const uint64_t r = (i - 1) >> 3, b = (i - 1) & 7;  // B = 8
+  const uint64_t r = (i - 1) / a.B, b = (i - 1) % a.B;
   const uint64_t chunk = (Q >> 5) * (a.R + 31) + r + (Q & 31);
-  return a.T[chunk * 256 + (b >> 2) * 128 + (Q & 31) * 4 + (b & 3)];
+  return a.T[chunk * 32 * a.B + (b >> 2) * 128 + (Q & 31) * 4 + (b & 3)];
 }
 
 __device__ __forceinline__ uint32_t p_word(const TraceArgs& a, uint32_t code, int64_t q) {
