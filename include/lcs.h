@@ -96,6 +96,24 @@ LCS_API int lcs_length(lcs_ctx* ctx, const uint8_t* x, uint64_t m, const uint8_t
 LCS_API int lcs_length_dev(lcs_ctx* ctx, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, uint64_t n,
                    uint64_t* d_out_len, void* stream);
 
+/* LCS length of two device strings without allocating any device memory. This entry point is an addition of the
+ * library; the paper has no counterpart. It is meant for callers that must not allocate device memory: code that
+ * runs inside a framework owning the whole device-memory pool or a fixed memory budget (an allocation there would
+ * fragment the pool or exceed the budget), and latency-critical loops, where cudaMalloc/cudaFree would synchronise
+ * the device and stall work on other streams.
+ *   - Limit: m, n <= 65536; larger sizes are rejected with LCS_ERR_INVALID.
+ *   - Scratch: a 6.5 MiB array that the library reserves statically in device memory. Every GPU that loads the
+ *     library holds it until the process exits. The first call on a device, made with that device current, looks up
+ *     the array's device address; make that first call before any stream capture.
+ *   - The array is shared by all calls on a device and keeps the last call's contents (each call clears what must
+ *     start at zero). Calls that overlapped on the GPU would race on it; this entry point therefore serialises its
+ *     calls per device and waits for each one.
+ *   - d_x, d_y and d_out_len are device pointers owned by the caller. The work is enqueued on `stream` (NULL = the
+ *     default stream); the call returns after the stream has finished it, with c[m,n] in *d_out_len on LCS_OK.
+ *   - Errors: LCS_ERR_INVALID, LCS_ERR_CUDA, LCS_ERR_TIMEOUT. */
+LCS_API int lcs_length_noalloc(const uint8_t* d_x, uint64_t m, const uint8_t* d_y, uint64_t n, uint64_t* d_out_len,
+                               void* stream);
+
 /* ---- traceback (paper §I.C LCS-length with table b, then §I.D Print-LCS) -------------------------------------- */
 
 /* Host buffers. Writes the LCS (forward order) to out[0..len) and len to *out_len. out_cap >= min(m, n) is always
