@@ -72,18 +72,6 @@ __device__ __forceinline__ bool give_up(DevStatus* st, uint32_t it, uint32_t lim
   return false;
 }
 
-// Waits (all lanes together) for a tagged slot: global (relaxed, gpu scope) or shared (volatile).
-// Returns (gave_up << 32) | value.
-__device__ __noinline__ uint64_t spin_slot(const uint32_t* gp, uint32_t saddr, bool global, uint32_t want,
-                                           uint32_t tmask, DevStatus* st, uint32_t limit) {
-  for (uint32_t it = 0;; ++it) {
-    const uint32_t v = global ? ld_relaxed_gpu(gp) : lds_vol_u32(saddr);
-    if ((v & tmask) == want) return v;
-    if ((it & 63u) == 63u && give_up(st, it, limit, global ? 1u : 2u)) return (1ull << 32) | v;
-    __nanosleep(32);
-  }
-}
-
 // Waits (all lanes together) until the consumer of a shared-memory ring has consumed row-blocks below `need`.
 __device__ __noinline__ bool spin_ring_space(uint32_t cons_saddr, uint32_t need, DevStatus* st, uint32_t limit) {
   for (uint32_t it = 0;; ++it) {
@@ -133,28 +121,26 @@ struct Warp {
 struct Lane {
   uint32_t V;         // the lane's word of the current row vector
   uint32_t cout;      // carry bits produced in the last step (row 0 of the block at bit 31)
-  uint32_t win_cur;   // inbound global window: slot 32*floor(t/32) + lane
-  uint32_t win_next;  // the following 32 slots
-  uint32_t q0, q1;    // inbound ring slots requested two steps ahead (even / odd steps)
+  uint32_t win;       // inbound window of the current 32-step block t0 .. t0+31: slot t0 + lane
+  uint32_t win_next;  // the next block's window, requested in the middle of the current block
   uint32_t cap;       // V captured at the end of this lane's row-block r with (r + 1) % 32 == 0 in this block
-  uint32_t xstage[16];  // symbol offsets of row-block t0 + 33 + lane, staged for the next 32-step boundary
+  uint32_t xstage[16];  // symbol offsets of row-block t0 + 34 + lane, staged for the next 32-step boundary
   uint4* tp;          // this step's bitmap chunk of the warp, plus this lane's offset
   bool failed;
 };
 
-// The B rows of one step. KT selects the row form: 0 = U = V & P; S = V + U + c; V' = S | (V & ~P) (three
-// dependent operations per row); 1 = the same values with V & ~P carried from the previous row, so that V' and
-// the next row's U come from S in one operation each (two dependent operations per row).
+// The B rows of one step, given the match masks P of the rows. KT selects the row form: 0 = U = V & P;
+// S = V + U + c; V' = S | (V & ~P) (three dependent operations per row); 1 = the same values with V & ~P carried
+// from the previous row, so that V' and the next row's U come from S in one operation each.
 template <int B, bool TB, int KT>
-__device__ __forceinline__ void rows(uint32_t peq_lane, const uint32_t (&xo)[B], uint32_t& V, uint32_t cin,
-                                     uint32_t& co, uint32_t (&tw)[B]) {
+__device__ __forceinline__ void rows(const uint32_t (&P)[B], uint32_t& V, uint32_t cin, uint32_t& co,
+                                     uint32_t (&tw)[B]) {
   uint32_t cw = cin;
   co = 0;
   if (KT == 0) {
 #pragma unroll
     for (int b = 0; b < B; ++b) {
-      const uint32_t P = lds_u32(peq_lane + xo[b]);
-      const uint32_t U = V & P;
+      const uint32_t U = V & P[b];
       uint32_t S;
       asm("add.cc.u32 %0, %0, %0;\n\t"
           "addc.cc.u32 %1, %3, %4;\n\t"
@@ -162,12 +148,9 @@ __device__ __forceinline__ void rows(uint32_t peq_lane, const uint32_t (&xo)[B],
           : "+r"(cw), "=r"(S), "+r"(co)
           : "r"(V), "r"(U));
       if (TB) tw[b] = S ^ V ^ U;
-      V = S | (V & ~P);
+      V = S | (V & ~P[b]);
     }
   } else {
-    uint32_t P[B];
-#pragma unroll
-    for (int b = 0; b < B; ++b) P[b] = lds_u32(peq_lane + xo[b]);
     uint32_t U = V & P[0], N = V & ~P[0];
 #pragma unroll
     for (int b = 0; b < B; ++b) {
@@ -194,51 +177,51 @@ __device__ __forceinline__ void rows(uint32_t peq_lane, const uint32_t (&xo)[B],
   }
 }
 
-// One step of one warp: lane l updates its word over the B rows of row-block r = t - l. Every load of the step
-// was issued at least one step earlier; the only lane-dependent work (lane 0 taking the previous warp's carries,
-// lane 31 handing its carries on, snapshots) is predicated, so the warp never diverges in the common case.
-template <int B, bool TB, int KT, bool SNAP, int SRC, int DST, int PAR>
-__device__ __forceinline__ void fill_step(const Warp& w, Lane& s, int32_t t, const uint32_t (&xo)[B],
-                                          uint32_t (&xn)[B]) {
+// Symbol offsets of row-block rb from the warp's shared ring (B words).
+template <int B>
+__device__ __forceinline__ void xo_from_ring(const Warp& w, int32_t rb, uint32_t (&dst)[B]) {
+  const uint32_t a = w.xring + ((uint32_t)rb & 63u) * (B * 4);
+#pragma unroll
+  for (int v = 0; v < B / 4; ++v) {
+    uint32_t q0, q1, q2, q3;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(q0), "=r"(q1), "=r"(q2), "=r"(q3) : "r"(a + 16 * v));
+    dst[4 * v] = q0;
+    dst[4 * v + 1] = q1;
+    dst[4 * v + 2] = q2;
+    dst[4 * v + 3] = q3;
+  }
+}
+
+// Match masks of the B rows whose symbol offsets are xo, for this lane's word.
+template <int B>
+__device__ __forceinline__ void p_from_offsets(const Warp& w, const uint32_t (&xo)[B], uint32_t (&P)[B]) {
+#pragma unroll
+  for (int b = 0; b < B; ++b) P[b] = lds_u32(w.peq_lane + xo[b]);
+}
+
+// One step of one warp: lane l updates its word over the B rows of row-block r = t - l, with the match masks pu
+// loaded during the previous step. During this step it loads the next step's match masks (from the offsets xa it
+// already holds) and the offsets of the step after that, so no step waits on a load. Lane 0 takes the previous
+// warp's carries from the block's window (validated once per block), lane 31 hands its own on; the step has no
+// branches.
+template <int B, bool TB, int KT, bool SNAP, int SRC, int DST>
+__device__ __forceinline__ void fill_step(const Warp& w, Lane& s, int32_t t, const uint32_t (&pu)[B],
+                                          const uint32_t (&xa)[B], uint32_t (&pl)[B], uint32_t (&xl)[B]) {
   constexpr uint32_t kTagMask = (1u << (32 - B)) - 1u;
   const uint32_t lane = w.lane;
   const int32_t r = t - (int32_t)lane;
-  {  // symbol offsets of the next step's row-block (t + 1 - lane) from the warp's shared ring
-    const uint32_t a = w.xring + (((uint32_t)(r + 1)) & 63u) * (B * 4);
-#pragma unroll
-    for (int v = 0; v < B / 4; ++v) {
-      uint32_t q0, q1, q2, q3;
-      asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(q0), "=r"(q1), "=r"(q2), "=r"(q3) : "r"(a + 16 * v));
-      xn[4 * v] = q0;
-      xn[4 * v + 1] = q1;
-      xn[4 * v + 2] = q2;
-      xn[4 * v + 3] = q3;
-    }
-  }
+  p_from_offsets<B>(w, xa, pl);
+  xo_from_ring<B>(w, r + 2, xl);
   const uint32_t c_up = __shfl_up_sync(kFull, s.cout, 1);
   uint32_t cin0 = 0;
   if (SRC != kSrcNone) {
-    uint32_t src;  // the same value in every lane
-    if (SRC == kSrcGlobal) {
-      src = __shfl_sync(kFull, s.win_cur, t & 31);
-    } else {
-      src = PAR ? s.q1 : s.q0;
-      const uint32_t nq = lds_vol_u32(w.ring_src + (((uint32_t)t + 2u) & (kRing - 1)) * 4u);
-      if (PAR) s.q1 = nq; else s.q0 = nq;
-    }
-    const uint32_t want = ((uint32_t)(t + 1) | 1u) & kTagMask;
-    if (t < w.R && (src & kTagMask) != want && !s.failed) {  // warp-uniform, rare after the first steps
-      const uint64_t res = spin_slot(w.src_g + t, w.ring_src + ((uint32_t)t & (kRing - 1)) * 4u,
-                                     SRC == kSrcGlobal, want, kTagMask, w.status, w.spin_limit);
-      src = (uint32_t)res;
-      s.failed = (res >> 32) != 0;
-    }
+    const uint32_t src = __shfl_sync(kFull, s.win, t & 31);
     cin0 = t < w.R ? (src & ~kTagMask) : 0u;
   }
   const uint32_t cin = lane == 0 ? cin0 : c_up;
   uint32_t co, V = s.V;
   uint32_t tw[B];
-  rows<B, TB, KT>(w.peq_lane, xo, V, cin, co, tw);
+  rows<B, TB, KT>(pu, V, cin, co, tw);
   s.V = V;
   s.cout = co << (32 - B);
   if (TB) {
@@ -280,14 +263,14 @@ __device__ __forceinline__ void xo_store_ring(const Warp& w, int32_t rb, const u
 }
 
 // Refill of the symbol-offset ring at a 32-step boundary t0: during steps t0 .. t0+31 the lanes read row-blocks
-// t0-30 .. t0+32; the ring (64 row-blocks) then holds t0-31 .. t0+32. The row-blocks t0+1 .. t0+32 were loaded
-// into registers at the previous boundary; the next ones are requested now and stored 32 steps later.
+// t0-29 .. t0+33 (two steps ahead); the 64-slot ring holds t0-30 .. t0+33 after this refill. Row-blocks t0+2 ..
+// t0+33 were loaded into registers at the previous boundary; the next 32 are requested now, stored 32 steps later.
 template <int B>
 __device__ __forceinline__ void xo_refill(const Warp& w, Lane& s, int32_t t0) {
   __syncwarp();
-  xo_store_ring<B>(w, t0 + 1 + (int32_t)w.lane, s.xstage);
+  xo_store_ring<B>(w, t0 + 2 + (int32_t)w.lane, s.xstage);
   __syncwarp();
-  xo_load_global<B>(w, t0 + 33 + (int32_t)w.lane, s.xstage);
+  xo_load_global<B>(w, t0 + 34 + (int32_t)w.lane, s.xstage);
 }
 
 // After the 32-step block starting at t0 (or the shorter last block ending at `end`): store the captured V when its
@@ -296,6 +279,41 @@ __device__ __forceinline__ void snap_store(const Warp& w, const Lane& s, int32_t
   const int32_t r = t0 + (int32_t)w.cap_k - (int32_t)w.lane;
   if (t0 + (int32_t)w.cap_k < end && r >= 0 && r < w.R && ((uint32_t)(r + 1) % w.snap_rb) == 0)
     w.snap[(uint64_t)((uint32_t)(r + 1) / w.snap_rb - 1) * w.wpad] = s.cap;
+}
+
+// Inbound window slot q (lane-specific) from the previous warp: global slots or the shared ring.
+template <int SRC>
+__device__ __forceinline__ uint32_t window_load(const Warp& w, int32_t q) {
+  if (SRC == kSrcGlobal) return q < w.R ? ld_relaxed_gpu(w.src_g + q) : 0u;
+  return lds_vol_u32(w.ring_src + ((uint32_t)q & (kRing - 1)) * 4u);
+}
+
+// Start of the 32-step block t0: switch to the window requested in the middle of the last block and make sure
+// every slot this block needs has arrived (all lanes together; a bounded wait in the rare case one has not).
+template <int B, int SRC>
+__device__ __forceinline__ void window_validate(const Warp& w, Lane& s, int32_t t0, bool first) {
+  if (SRC == kSrcNone) return;
+  constexpr uint32_t kTagMask = (1u << (32 - B)) - 1u;
+  if (!first) s.win = s.win_next;
+  const int32_t q = t0 + (int32_t)w.lane;
+  const uint32_t want = ((uint32_t)(q + 1) | 1u) & kTagMask;
+  bool ok = q >= w.R || (s.win & kTagMask) == want;
+  if (__all_sync(kFull, ok) || s.failed) return;
+  for (uint32_t it = 0;; ++it) {
+    if (!ok) {
+      s.win = window_load<SRC>(w, q);
+      ok = (s.win & kTagMask) == want;
+    }
+    if (__all_sync(kFull, ok)) return;
+    if ((it & 63u) == 63u) {
+      const bool quit = __any_sync(kFull, give_up(w.status, it, w.spin_limit, SRC == kSrcGlobal ? 1u : 2u));
+      if (quit) {
+        s.failed = true;
+        return;
+      }
+    }
+    __nanosleep(32);
+  }
 }
 
 // Work at the start of each 32-step block: publish consumption, honour ring back-pressure.
@@ -312,55 +330,46 @@ __device__ __forceinline__ void block_start(const Warp& w, Lane& s, int32_t t) {
 
 template <int B, bool TB, int KT, bool SNAP, int SRC, int DST>
 __device__ __forceinline__ void warp_loop(const Warp& w, Lane& s) {
-  uint32_t xa[B], xb[B];
-  {  // ring: row-blocks -31 .. 0 now, 1 .. 32 at the first boundary (t0 = 0), 33 .. 64 staged
-    uint32_t tmp[B];
-    xo_load_global<B>(w, -31 + (int32_t)w.lane, tmp);
-    xo_store_ring<B>(w, -31 + (int32_t)w.lane, tmp);
-    xo_load_global<B>(w, 1 + (int32_t)w.lane, s.xstage);
-    __syncwarp();
-    const uint32_t a = w.xring + ((uint32_t)(-(int32_t)w.lane) & 63u) * (B * 4);  // row-block -lane, step 0
-#pragma unroll
-    for (int v = 0; v < B / 4; ++v) {
-      uint32_t q0, q1, q2, q3;
-      asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(q0), "=r"(q1), "=r"(q2), "=r"(q3) : "r"(a + 16 * v));
-      xa[4 * v] = q0;
-      xa[4 * v + 1] = q1;
-      xa[4 * v + 2] = q2;
-      xa[4 * v + 3] = q3;
-    }
-    xo_refill<B>(w, s, 0);
-  }
+  const int32_t lane = (int32_t)w.lane;
+  uint32_t x0[B], x1[B], p0[B], p1[B];
+  // ring: row-blocks -30 .. 1 now (block 0 reads -29 .. 33), 2 .. 33 at the first boundary, 34 .. 65 staged
+  xo_load_global<B>(w, -30 + lane, s.xstage);
+  xo_store_ring<B>(w, -30 + lane, s.xstage);
+  xo_load_global<B>(w, 2 + lane, s.xstage);
+  xo_load_global<B>(w, -lane, x0);     // step 0's row-block
+  xo_load_global<B>(w, 1 - lane, x1);  // step 1's row-block
+  __syncwarp();
+  p_from_offsets<B>(w, x0, p0);
+  if (SRC != kSrcNone) s.win = window_load<SRC>(w, lane);
   const int32_t steps = w.R + 31;
   int32_t t = 0;
+  // pipeline at an even step t: p0 = masks of step t, x1 = offsets of step t+1
   for (; t + 32 <= steps; t += 32) {
-    if (t) xo_refill<B>(w, s, t);
+    xo_refill<B>(w, s, t);
+    window_validate<B, SRC>(w, s, t, t == 0);
     block_start<SRC, DST>(w, s, t);
 #pragma unroll 1
     for (int k = 0; k < 16; k += 2) {
-      fill_step<B, TB, KT, SNAP, SRC, DST, 0>(w, s, t + k, xa, xb);
-      fill_step<B, TB, KT, SNAP, SRC, DST, 1>(w, s, t + k + 1, xb, xa);
+      fill_step<B, TB, KT, SNAP, SRC, DST>(w, s, t + k, p0, x1, p1, x0);
+      fill_step<B, TB, KT, SNAP, SRC, DST>(w, s, t + k + 1, p1, x0, p0, x1);
     }
-    if (SRC == kSrcGlobal) {  // the next window, 16 steps before it is needed
-      const int32_t q = t + 32 + (int32_t)w.lane;
-      s.win_next = q < w.R ? ld_relaxed_gpu(w.src_g + q) : 0u;
-    }
+    if (SRC != kSrcNone) s.win_next = window_load<SRC>(w, t + 32 + lane);  // the next block's window
 #pragma unroll 1
     for (int k = 16; k < 32; k += 2) {
-      fill_step<B, TB, KT, SNAP, SRC, DST, 0>(w, s, t + k, xa, xb);
-      fill_step<B, TB, KT, SNAP, SRC, DST, 1>(w, s, t + k + 1, xb, xa);
+      fill_step<B, TB, KT, SNAP, SRC, DST>(w, s, t + k, p0, x1, p1, x0);
+      fill_step<B, TB, KT, SNAP, SRC, DST>(w, s, t + k + 1, p1, x0, p0, x1);
     }
-    if (SRC == kSrcGlobal) s.win_cur = s.win_next;
     if (SNAP) snap_store(w, s, t, steps);
   }
-  if (t) xo_refill<B>(w, s, t);
+  xo_refill<B>(w, s, t);
+  window_validate<B, SRC>(w, s, t, t == 0);
   block_start<SRC, DST>(w, s, t);
   const int32_t t_tail = t;
   for (; t + 1 < steps; t += 2) {
-    fill_step<B, TB, KT, SNAP, SRC, DST, 0>(w, s, t, xa, xb);
-    fill_step<B, TB, KT, SNAP, SRC, DST, 1>(w, s, t + 1, xb, xa);
+    fill_step<B, TB, KT, SNAP, SRC, DST>(w, s, t, p0, x1, p1, x0);
+    fill_step<B, TB, KT, SNAP, SRC, DST>(w, s, t + 1, p1, x0, p0, x1);
   }
-  if (t < steps) fill_step<B, TB, KT, SNAP, SRC, DST, 0>(w, s, t, xa, xb);
+  if (t < steps) fill_step<B, TB, KT, SNAP, SRC, DST>(w, s, t, p0, x1, p1, x0);
   if (SNAP) snap_store(w, s, t_tail, steps);
 }
 
@@ -427,10 +436,8 @@ __global__ void __launch_bounds__(kFillThreads, 1) k_fill(const __grid_constant_
   s.cap = 0;
   w.snap = J.snap ? J.snap + gw * 32 + lane : nullptr;
   w.cap_k = (lane + 31u) & 31u;
-  s.win_cur = (wib == 0 && !first_warp && (int32_t)lane < w.R) ? ld_relaxed_gpu(w.src_g + lane) : 0u;
+  s.win = 0;
   s.win_next = 0;
-  s.q0 = 0;
-  s.q1 = 0;
   s.tp = J.T ? reinterpret_cast<uint4*>(J.T + (gw * (J.R + 31)) * 32 * (uint64_t)B) + lane : nullptr;
 
   if (TB && J.T) {
