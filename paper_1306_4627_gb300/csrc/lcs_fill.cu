@@ -106,6 +106,8 @@ struct Warp {
   uint32_t cons_self;  // this warp's consumption counter (read by the producer for back-pressure)
   uint32_t cons_next;  // the next warp's consumption counter
   uint32_t xring;     // shared-memory ring of symbol offsets: row-block rb at slot rb % 64 (B words each)
+  const uint4* xring_p;  // the same ring, laid out [B/4][64 slots] of 16-byte vectors (bank-conflict free)
+  const uint32_t* peq_p;  // this lane's column of the match masks (row s at peq_p[s * kStripeWords])
   const uint32_t* xoff;  // global symbol offsets: row-block rb at xoff + (rb + kPadRowblocks) * B
   const uint32_t* src_g;
   uint32_t* dst_g;
@@ -177,26 +179,26 @@ __device__ __forceinline__ void rows(const uint32_t (&P)[B], uint32_t& V, uint32
   }
 }
 
-// Symbol offsets of row-block rb from the warp's shared ring (B words).
+// Symbol offsets of row-block rb from the warp's shared ring (B words). The ring is laid out [B/4][64] in 16-byte
+// vectors, so the 32 lanes (consecutive row-blocks) read 32 consecutive vectors: no bank conflicts.
 template <int B>
 __device__ __forceinline__ void xo_from_ring(const Warp& w, int32_t rb, uint32_t (&dst)[B]) {
-  const uint32_t a = w.xring + ((uint32_t)rb & 63u) * (B * 4);
+  const uint32_t slot = (uint32_t)rb & 63u;
 #pragma unroll
   for (int v = 0; v < B / 4; ++v) {
-    uint32_t q0, q1, q2, q3;
-    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(q0), "=r"(q1), "=r"(q2), "=r"(q3) : "r"(a + 16 * v));
-    dst[4 * v] = q0;
-    dst[4 * v + 1] = q1;
-    dst[4 * v + 2] = q2;
-    dst[4 * v + 3] = q3;
+    const uint4 q = w.xring_p[v * 64 + slot];
+    dst[4 * v] = q.x;
+    dst[4 * v + 1] = q.y;
+    dst[4 * v + 2] = q.z;
+    dst[4 * v + 3] = q.w;
   }
 }
 
-// Match masks of the B rows whose symbol offsets are xo, for this lane's word.
+// Match masks of the B rows whose symbol offsets are xo (in words), for this lane's word.
 template <int B>
 __device__ __forceinline__ void p_from_offsets(const Warp& w, const uint32_t (&xo)[B], uint32_t (&P)[B]) {
 #pragma unroll
-  for (int b = 0; b < B; ++b) P[b] = lds_u32(w.peq_lane + xo[b]);
+  for (int b = 0; b < B; ++b) P[b] = w.peq_p[xo[b]];
 }
 
 // One step of one warp: lane l updates its word over the B rows of row-block r = t - l, with the match masks pu
@@ -254,12 +256,10 @@ __device__ __forceinline__ void xo_load_global(const Warp& w, int32_t rb, uint32
 }
 template <int B>
 __device__ __forceinline__ void xo_store_ring(const Warp& w, int32_t rb, const uint32_t* src) {
-  const uint32_t a = w.xring + ((uint32_t)rb & 63u) * (B * 4);
+  uint4* ring = const_cast<uint4*>(w.xring_p);
+  const uint32_t slot = (uint32_t)rb & 63u;
 #pragma unroll
-  for (int v = 0; v < B / 4; ++v)
-    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(a + 16 * v), "r"(src[4 * v]), "r"(src[4 * v + 1]),
-                 "r"(src[4 * v + 2]), "r"(src[4 * v + 3])
-                 : "memory");
+  for (int v = 0; v < B / 4; ++v) ring[v * 64 + slot] = make_uint4(src[4 * v], src[4 * v + 1], src[4 * v + 2], src[4 * v + 3]);
 }
 
 // Refill of the symbol-offset ring at a 32-step boundary t0: during steps t0 .. t0+31 the lanes read row-blocks
@@ -423,6 +423,8 @@ __global__ void __launch_bounds__(kFillThreads, 1) k_fill(const __grid_constant_
   w.dst_g = J.carry + (uint64_t)blk * J.R;
   w.peq_lane = (uint32_t)__cvta_generic_to_shared(peq_s) + (wib * 32 + lane) * 4u;
   w.xring = (uint32_t)__cvta_generic_to_shared(xring + wib * 64 * B);
+  w.xring_p = reinterpret_cast<const uint4*>(xring + wib * 64 * B);
+  w.peq_p = peq_s + wib * 32 + lane;
   w.xoff = J.xoff;
   w.ring_src = (uint32_t)__cvta_generic_to_shared(ring + (wib == 0 ? 0 : wib - 1) * kRing);
   w.ring_dst = (uint32_t)__cvta_generic_to_shared(ring + (wib + 1 < kFillWarps ? wib : 0) * kRing);

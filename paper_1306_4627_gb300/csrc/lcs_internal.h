@@ -33,7 +33,7 @@ struct DevStatus {
 
 // One DP problem for the fill kernel (a forward table, or the table of the reversed strings).
 struct FillJob {
-  const uint32_t* xoff;     // per padded row: byte offset of its symbol's row in the block's shared Peq stripe;
+  const uint32_t* xoff;     // per padded row: word offset of its symbol's row in the block's shared Peq stripe;
                             // (kPadRowblocks + R + kPadBackRowblocks) * B entries
   const uint32_t* peq;      // match masks [sigma row][wpad], row 'sigma' (the last) all zero
   const uint32_t* sigma_rows;  // device word: rows of peq in use (present symbols + 1)

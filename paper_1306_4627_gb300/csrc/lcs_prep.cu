@@ -49,7 +49,7 @@ __global__ void k_xoff(const uint8_t* __restrict__ x, uint64_t m, int reverse, u
       code = codemap[x[reverse ? (m - 1 - i) : i]];
       if (xcode) xcode[i] = (uint8_t)code;
     }
-    xoff[p] = code * (uint32_t)(kStripeWords * 4);
+    xoff[p] = code * (uint32_t)kStripeWords;  // word offset of the symbol's row in a block's match-mask stripe
   }
 }
 
