@@ -286,6 +286,139 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def alu_peak_tops(sm_mhz: float, sms: int = 152) -> float:
+    """INT32 ALU peak from unit counts and clock: 64 INT32 lanes per SM per clock (LOP3/IADD3) x SMs x clock."""
+    return sms * 64 * sm_mhz * 1e6 / 1e12
+
+
+def run_batch_workload(args):
+    """10000 independent pairs (m, n log-uniform in [64, 4096]; alphabet 4 for half, 20 for the other half),
+    lengths only, one persistent launch per step; plus the same pairs as sequential single-pair launches."""
+    import torch
+    from paper_1306_4627_gb300 import gen, lcs
+    dev = torch.device("cuda", 0)
+    pairs = gen.batch_pairs()
+    xs = np.concatenate([x for x, _ in pairs])
+    ys = np.concatenate([y for _, y in pairs])
+    xo = np.zeros(len(pairs) + 1, np.int64)
+    yo = np.zeros(len(pairs) + 1, np.int64)
+    xo[1:] = np.cumsum([len(x) for x, _ in pairs])
+    yo[1:] = np.cumsum([len(y) for _, y in pairs])
+    cells = int(sum(len(x) * len(y) for x, y in pairs))
+    dxs, dys = torch.from_numpy(xs).to(dev), torch.from_numpy(ys).to(dev)
+    dxo, dyo = torch.from_numpy(xo).to(dev), torch.from_numpy(yo).to(dev)
+    out = torch.zeros(len(pairs), dtype=torch.int64, device=dev)
+    ctx = lcs.Context(0)
+    stream = torch.cuda.Stream(device=dev)
+    ctx.set_profiling(True)
+    for _ in range(args.warmup):
+        ctx.batch_dev(dxs, dxo, dys, dyo, len(pairs), out, stream=stream)
+    ctx.sync()
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    tot, kern, prep = [], [], []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.batch_dev(dxs, dxo, dys, dyo, len(pairs), out, stream=stream)
+        p = ctx.last_profile()
+        tot.append(time.perf_counter() - t0)
+        kern.append(p["fill_ms"])
+        prep.append(p["prep_ms"])
+    clocks = sampler.stop()
+    ctx.sync()
+    # host-buffer end to end
+    e2e = []
+    ctx.set_profiling(False)
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        ctx.batch(pairs)
+        if k >= args.warmup:
+            e2e.append(time.perf_counter() - t0)
+    # sequential per-pair launches on a sample of the pairs (lcs_length_dev, one pair at a time)
+    sample = list(range(0, len(pairs), max(1, len(pairs) // args.seq_sample)))
+    dx1 = [torch.from_numpy(pairs[i][0].copy()).to(dev) for i in sample]
+    dy1 = [torch.from_numpy(pairs[i][1].copy()).to(dev) for i in sample]
+    o1 = torch.zeros(1, dtype=torch.int64, device=dev)
+    for a, b in zip(dx1[:5], dy1[:5]):
+        ctx.length_dev(a, b, o1)
+    ctx.sync()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for a, b in zip(dx1, dy1):
+        ctx.length_dev(a, b, o1)
+    ctx.sync()
+    seq_s = time.perf_counter() - t0
+    seq_cells = sum(len(pairs[i][0]) * len(pairs[i][1]) for i in sample)
+    t_ms = float(np.median(tot)) * 1e3
+    k_ms = float(np.median(kern))
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    peak = alu_peak_tops(sm_mhz)
+    achieved = cells / 32 * 4 / (k_ms * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": cells / (t_ms * 1e-3) / 1e9, "unit": "GCUPS", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "batch: 10000 pairs, m and n log-uniform in [64, 4096], sigma 4 (half) and 20 (half), "
+                               "lengths only", "cells": cells, "pairs": len(pairs)},
+        "stages_ms": {"prep": float(np.median(prep)), "batch_kernel": k_ms},
+        "kernel_gcups": cells / (k_ms * 1e-3) / 1e9,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "k_batch_main",
+                     "note": "algorithmic work = 4 INT32 ops per 32 cells; peak = 152 SMs x 64 INT32/clk x sampled "
+                             "SM clock"},
+        "sequential_per_pair": {"gcups": seq_cells / seq_s / 1e9, "pairs_timed": len(sample),
+                                "note": "lcs_length_dev per pair, back to back, same GPU"},
+        "e2e": {"value": cells / float(np.median(e2e)) / 1e9, "unit": "GCUPS",
+                "h2d_bytes_per_step": int(xs.nbytes + ys.nbytes), "d2h_bytes_per_step": 8 * len(pairs)},
+        "gpu_launches": 2 * args.steps, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_long_workload(args):
+    """One length-only pair of m = n = 262144 (alphabet 4 and 20)."""
+    import torch
+    from paper_1306_4627_gb300 import gen, lcs
+    dev = torch.device("cuda", 0)
+    res = {}
+    ctx = lcs.Context(0)
+    ctx.set_profiling(True)
+    stream = torch.cuda.Stream(device=dev)
+    for sigma in (4, 20):
+        x, y = gen.pair_uniform(262144, 262144, sigma, seed=gen.BASE_SEED + 2)
+        dx, dy = torch.from_numpy(x.copy()).to(dev), torch.from_numpy(y.copy()).to(dev)
+        out = torch.zeros(1, dtype=torch.int64, device=dev)
+        for _ in range(args.warmup):
+            ctx.length_dev(dx, dy, out, stream=stream)
+        ctx.sync()
+        ts, fs = [], []
+        for _ in range(args.steps):
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            ctx.length_dev(dx, dy, out, stream=stream)
+            ev1.record(stream)
+            p = ctx.last_profile()
+            ev1.synchronize()
+            ts.append(ev0.elapsed_time(ev1))
+            fs.append(p["fill_ms"])
+        res[sigma] = (float(np.median(ts)), float(np.median(fs)), int(out.item()))
+    cells = 262144 ** 2
+    t4 = res[4][0]
+    line = {
+        "metric": METRIC, "value": cells / (t4 * 1e-3) / 1e9, "unit": "GCUPS", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t4, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "single pair, length only, m=n=262144, sigma 4 (value) and 20",
+                   "sigma20_gcups": cells / (res[20][0] * 1e-3) / 1e9, "lcs_length": {4: res[4][2], 20: res[20][2]}},
+        "stages_ms": {"fill_sigma4": res[4][1], "fill_sigma20": res[20][1]},
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     global M, N
     ap = argparse.ArgumentParser()
@@ -299,12 +432,19 @@ def main():
     ap.add_argument("--m", type=int, default=M, help="rows (profiling of smaller cases only)")
     ap.add_argument("--n", type=int, default=N, help="columns (profiling of smaller cases only)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="pair", choices=["pair", "batch", "long"],
+                    help="pair: the 65536^2 traceback step (default); batch: 10000 pairs; long: 262144^2 length")
+    ap.add_argument("--seq-sample", type=int, default=400, help="pairs timed as sequential single-pair launches")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     M, N = args.m, args.n
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch_workload(args)
+    elif args.workload == "long":
+        run_long_workload(args)
     else:
         run_gpu(args)
 

@@ -70,8 +70,9 @@ LCS_API int lcs_ctx_sync(lcs_ctx* ctx);
  * The paper times its method with omp_get_wtime around the whole computation (§II.A, steps 6 and 21, EXEC_TIME).
  * Here every stage of the last length/traceback call is timed with CUDA events recorded on the call's stream. */
 typedef struct lcs_profile {
-  double prep_ms;        /* alphabet, match masks and per-row symbol offsets */
-  double fill_ms;        /* the table fill kernel (all rows; both tables when the reversed strings run too) */
+  double prep_ms;        /* alphabet, match masks and per-row symbol offsets (per pair for lcs_batch) */
+  double fill_ms;        /* the table fill kernel (all rows; both tables when the reversed strings run too);
+                            for lcs_batch, the persistent batch kernel */
   double trace_ms;       /* corridors, segment walks, chain and output assembly (0 for length-only calls) */
   double total_ms;       /* first stage start to last stage end */
   uint64_t fill_blocks;  /* thread blocks of the fill launch */

@@ -24,6 +24,7 @@ constexpr size_t kOffSigma = 544;      // uint32_t
 constexpr size_t kOffLenAcc = 552;     // unsigned long long
 constexpr size_t kOffStatus = 576;     // DevStatus (16 B)
 constexpr size_t kOffOutLen = 608;     // uint64_t
+constexpr size_t kOffTicket = 640;     // uint32_t work ticket of the persistent batch kernel
 constexpr size_t kSmallBytes = 1024;
 
 }  // namespace lcs
@@ -39,6 +40,7 @@ struct lcs_ctx {
   lcs::DBuf small, x, y, out;
   lcs::DBuf xoff_f, xoff_r, xcode, peq_f, peq_r, carry_f, carry_r, fv_f, fv_r, T, snap_f, snap_r;
   lcs::DBuf colsum, ent, ext, nch, entcnt, sel, chars;
+  lcs::DBuf bplan, bsig, bxcode, bpeq, bout;  // batch: plan, per-pair alphabet sizes, codes, masks, lengths
   uint64_t host_word[1] = {0};
   // stage events of the last profiled call: [0] start, [1] fill start, [2] fill end, [3] end
   bool prof = false, prof_valid = false, prof_trace = false;
@@ -57,7 +59,8 @@ struct lcs_ctx {
 
   void release_all() {
     lcs::DBuf* all[] = {&small, &x, &y, &out, &xoff_f, &xoff_r, &xcode, &peq_f, &peq_r, &carry_f, &carry_r,
-                        &fv_f, &fv_r, &T, &snap_f, &snap_r, &colsum, &ent, &ext, &nch, &entcnt, &sel, &chars};
+                        &fv_f, &fv_r, &T, &snap_f, &snap_r, &colsum, &ent, &ext, &nch, &entcnt, &sel, &chars,
+                        &bplan, &bsig, &bxcode, &bpeq, &bout};
     for (lcs::DBuf* b : all) lcs::release(*b);
   }
 };

@@ -1,0 +1,82 @@
+"""lcs_batch: many independent pairs in one persistent launch, every length exact vs the CPU oracle."""
+
+import numpy as np
+import pytest
+
+from paper_1306_4627_gb300 import gen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1306_4627_gb300 import lcs
+    c = lcs.Context(0)
+    yield c
+    c.close()
+
+
+def test_batch_edge_shapes(ctx, oracle):
+    shapes = [(0, 5), (5, 0), (1, 1), (1, 31), (31, 32), (33, 33), (64, 127), (100, 128), (129, 129), (7, 512),
+              (513, 1000), (2000, 4096), (300, 4097), (50, 5000), (4096, 64)]
+    pairs = []
+    for k, (m, n) in enumerate(shapes):
+        pairs.append(gen.pair_uniform(m, n, 4, seed=900 + k))
+    got = ctx.batch(pairs)
+    for (x, y), g in zip(pairs, got):
+        assert int(g) == oracle.lcs_length(x, y), (len(x), len(y))
+
+
+@pytest.mark.parametrize("sigma", [2, 4, 20, 256])
+def test_batch_random_mixed(ctx, oracle, sigma):
+    rng = np.random.default_rng(sigma)
+    pairs = []
+    for k in range(300):
+        m = int(rng.integers(1, 700))
+        n = int(rng.integers(1, 1500))
+        alpha = {2: b"AB", 4: gen.DNA, 20: gen.PROTEIN, 256: gen.BYTES}[sigma]
+        pairs.append((gen.random_string(5000 + 2 * k, m, alpha), gen.random_string(5001 + 2 * k, n, alpha)))
+    got = ctx.batch(pairs)
+    want = [oracle.lcs_length(x, y) for x, y in pairs]
+    assert [int(v) for v in got] == want
+
+
+def test_batch_mixed_alphabets_in_one_launch(ctx, oracle):
+    pairs = [gen.pair_uniform(200 + 13 * k, 3000 - 11 * k, [4, 20, 256][k % 3], seed=70 + k) for k in range(60)]
+    got = ctx.batch(pairs)
+    assert [int(v) for v in got] == [oracle.lcs_length(x, y) for x, y in pairs]
+
+
+def test_batch_dev_matches_host(ctx):
+    import torch
+    pairs = gen.batch_pairs(count=500, seed=123)
+    host = ctx.batch(pairs)
+    xs = np.concatenate([x for x, _ in pairs])
+    ys = np.concatenate([y for _, y in pairs])
+    xo = np.zeros(len(pairs) + 1, np.int64)
+    yo = np.zeros(len(pairs) + 1, np.int64)
+    xo[1:] = np.cumsum([len(x) for x, _ in pairs])
+    yo[1:] = np.cumsum([len(y) for _, y in pairs])
+    d = torch.device("cuda", 0)
+    out = torch.zeros(len(pairs), dtype=torch.int64, device=d)
+    ctx.batch_dev(torch.from_numpy(xs).to(d), torch.from_numpy(xo).to(d), torch.from_numpy(ys).to(d),
+                  torch.from_numpy(yo).to(d), len(pairs), out)
+    ctx.sync()
+    assert np.array_equal(out.cpu().numpy(), host.astype(np.int64))
+
+
+def test_batch_matches_single_pair_path(ctx):
+    pairs = gen.batch_pairs(count=200, seed=321)
+    got = ctx.batch(pairs)
+    for (x, y), g in zip(pairs[:60], got[:60]):
+        assert int(g) == ctx.length(x, y)
+
+
+@pytest.mark.slow
+def test_batch_10000_pairs_vs_oracle(ctx, oracle):
+    """The batched workload: 10000 pairs, m and n log-uniform in [64, 4096], alphabet 4 for half the pairs and
+    20 for the other half; every length exact vs the oracle."""
+    pairs = gen.batch_pairs()
+    got = ctx.batch(pairs)
+    want = np.array([oracle.lcs_length(x, y) for x, y in pairs])
+    assert np.array_equal(got.astype(np.int64), want)
