@@ -77,6 +77,7 @@ int run_fill(lcs_ctx* c, FillJob* jobs, int njobs, bool traceback, cudaStream_t 
   a.status = c->status();
   a.spin_limit = c->spin_limit;
   a.variant = c->fill_variant;
+  a.debug_drop = c->debug_drop;
   uint32_t total = 0;
   for (int k = 0; k < njobs; ++k) total += jobs[k].nblocks_total;
   if (total <= (uint32_t)c->max_coop) {
@@ -327,6 +328,9 @@ extern "C" int lcs_ctx_create(int device, lcs_ctx** out) {
   }
   if (const char* e = getenv("LCS_FILL_B")) c->fill_B = (atoi(e) == 16) ? 16u : 8u;
   if (const char* e = getenv("LCS_FILL_VARIANT")) c->fill_variant = (uint32_t)atoi(e);
+  // bounded-wait testing: a short wait limit and a carry hand-off that is never published
+  if (const char* e = getenv("LCS_SPIN_LIMIT")) c->spin_limit = (uint32_t)std::max(64, atoi(e));
+  if (const char* e = getenv("LCS_DEBUG_DROP_HANDOFF")) c->debug_drop = atoi(e) ? 1u : 0u;
   *out = c;
   return LCS_OK;
 }

@@ -36,6 +36,7 @@ struct lcs_ctx {
   uint32_t spin_limit = 1u << 22;
   uint32_t fill_B = 8;        // rows per systolic step (8 or 16)
   uint32_t fill_variant = 0;  // bit 0: shorter dependent chain per row
+  uint32_t debug_drop = 0;    // test hook (environment LCS_DEBUG_DROP_HANDOFF): a hand-off that never comes
   std::mutex mu;
   lcs::DBuf small, x, y, out;
   lcs::DBuf xoff_f, xoff_r, xcode, peq_f, peq_r, carry_f, carry_r, fv_f, fv_r, T, snap_f, snap_r;

@@ -117,6 +117,7 @@ struct Warp {
   int32_t R;
   uint32_t lane, snap_rb, spin_limit;
   uint32_t cap_k;     // step (mod 32) at which this lane finishes a row-block r with (r + 1) % 32 == 0
+  uint32_t hands_on;  // 1 for the lane that hands the warp's carries on (lane 31)
 };
 
 // Loop state of one lane, kept in registers across the unrolled steps.
@@ -235,7 +236,7 @@ __device__ __forceinline__ void fill_step(const Warp& w, Lane& s, int32_t t, con
   if (DST != kDstNone) {  // lane 31 hands its carries for row-block t - 31 to the next warp
     const uint32_t r31 = (uint32_t)(t - 31);
     const uint32_t v = s.cout | ((r31 + 1u) | 1u) & kTagMask;
-    const uint32_t pred = (lane == 31) & (t >= 31);
+    const uint32_t pred = w.hands_on & (t >= 31);
     if (DST == kDstGlobal) st_relaxed_gpu_if(w.dst_g + (int64_t)t - 31, v, pred);
     else sts_vol_u32_if(w.ring_dst + (r31 & (kRing - 1)) * 4u, v, pred);
   }
@@ -438,6 +439,7 @@ __global__ void __launch_bounds__(kFillThreads, 1) k_fill(const __grid_constant_
   s.cap = 0;
   w.snap = J.snap ? J.snap + gw * 32 + lane : nullptr;
   w.cap_k = (lane + 31u) & 31u;
+  w.hands_on = (lane == 31 && !(a.debug_drop && gw == 0)) ? 1u : 0u;
   s.win = 0;
   s.win_next = 0;
   s.tp = J.T ? reinterpret_cast<uint4*>(J.T + (gw * (J.R + 31)) * 32 * (uint64_t)B) + lane : nullptr;

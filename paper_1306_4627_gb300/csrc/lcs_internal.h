@@ -56,6 +56,7 @@ struct FillArgs {
   DevStatus* status;
   uint32_t spin_limit;      // iterations of a bounded wait before it gives up
   uint32_t variant;         // bit 0: shorter dependent chain per row (same results)
+  uint32_t debug_drop;      // test hook: the first warp never hands its carries on (its consumer's wait runs out)
 };
 
 // ---- traceback segment walkers ---------------------------------------------------------------------------------
