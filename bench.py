@@ -419,6 +419,72 @@ def run_long_workload(args):
     ctx.close()
 
 
+def run_serve_workload(args):
+    """Poisson request streams at swept rates: m and n log-uniform in [32, 65536], alphabet 4, 20 or 256, 20%
+    traceback. Latency (submit to result) is measured by the server; each rate also records the service time of
+    the same requests run one by one through the single-pair calls (the per-pair baseline)."""
+    from paper_1306_4627_gb300 import gen, lcs
+    ctx = lcs.Context(0)
+    rates = [float(r) for r in args.rates.split(",")]
+    out_rates = []
+    for rate in rates:
+        reqs = gen.serve_requests(rate=rate, count=args.serve_count, seed=gen.BASE_SEED + 4)
+        cells = sum(len(r["x"]) * len(r["y"]) for r in reqs)
+        srv = lcs.Server(ctx)
+        # warm the workers' buffers with a few requests
+        for r in reqs[:8]:
+            srv.wait(srv.submit(r["x"], r["y"], traceback=r["traceback"]), timeout_s=60.0)
+        tickets = []
+        t0 = time.perf_counter()
+        for r in reqs:
+            due = t0 + r["t"] - reqs[0]["t"]
+            while True:
+                now = time.perf_counter()
+                if now >= due:
+                    break
+                if due - now > 2e-4:
+                    time.sleep((due - now) * 0.5)
+            while True:
+                rc, t = srv.try_submit(r["x"], r["y"], traceback=r["traceback"])
+                if rc == lcs.OK:
+                    break
+                time.sleep(1e-4)  # back-pressure: retry
+            tickets.append(t)
+        lat = []
+        for t in tickets:
+            res = srv.wait(t, timeout_s=600.0)
+            lat.append(res["latency_s"])
+        wall = time.perf_counter() - t0
+        srv.close()
+        lat = np.array(lat)
+        out_rates.append({"rate_per_s": rate, "requests": len(reqs), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                          "p99_ms": float(np.percentile(lat, 99) * 1e3), "gcups": cells / wall / 1e9,
+                          "offered_gcups": cells / (reqs[-1]["t"] - reqs[0]["t"]) / 1e9, "wall_s": wall})
+        print(json.dumps({"serve_rate": out_rates[-1]}), file=sys.stderr, flush=True)
+    # per-pair baseline: the same request mix, one call at a time (service time of each)
+    reqs = gen.serve_requests(rate=1000.0, count=min(args.serve_count, 1000), seed=gen.BASE_SEED + 4)
+    svc = []
+    for r in reqs:
+        t1 = time.perf_counter()
+        (ctx.traceback if r["traceback"] else ctx.length)(r["x"], r["y"])
+        svc.append(time.perf_counter() - t1)
+    svc = np.array(svc)
+    best = max(out_rates, key=lambda d: d["gcups"])
+    line = {
+        "metric": METRIC, "value": best["gcups"], "unit": "GCUPS", "n_gpus": 1, "steps": len(rates),
+        "warmup": 1, "ms_per_step": best["wall_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "serving: Poisson arrivals, m,n log-uniform [32, 65536], sigma 4/20/256, 20% traceback",
+                   "requests_per_rate": args.serve_count},
+        "rates": out_rates,
+        "per_pair_baseline": {"p50_ms": float(np.percentile(svc, 50) * 1e3), "p99_ms": float(np.percentile(svc, 99) * 1e3),
+                              "gcups": sum(len(r["x"]) * len(r["y"]) for r in reqs) / svc.sum() / 1e9,
+                              "note": "each request alone through lcs_length / lcs_traceback, one at a time"},
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     global M, N
     ap = argparse.ArgumentParser()
@@ -432,9 +498,11 @@ def main():
     ap.add_argument("--m", type=int, default=M, help="rows (profiling of smaller cases only)")
     ap.add_argument("--n", type=int, default=N, help="columns (profiling of smaller cases only)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="pair", choices=["pair", "batch", "long"],
+    ap.add_argument("--workload", default="pair", choices=["pair", "batch", "long", "serve"],
                     help="pair: the 65536^2 traceback step (default); batch: 10000 pairs; long: 262144^2 length")
     ap.add_argument("--seq-sample", type=int, default=400, help="pairs timed as sequential single-pair launches")
+    ap.add_argument("--rates", default="1000,3000,10000,30000,100000", help="serving: request rates per second")
+    ap.add_argument("--serve-count", type=int, default=3000, help="serving: requests per rate")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -445,6 +513,8 @@ def main():
         run_batch_workload(args)
     elif args.workload == "long":
         run_long_workload(args)
+    elif args.workload == "serve":
+        run_serve_workload(args)
     else:
         run_gpu(args)
 
