@@ -157,6 +157,17 @@ def flush_l2(buf):
     buf.add_(1)  # writes 256 MiB (> 129 MB L2)
 
 
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """The slowest rank's time (a barrier first, then a MAX all-reduce); the value itself on one process."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.barrier()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_gpu(args):
     import torch
     ws, rank, local = dist_env()
@@ -211,12 +222,7 @@ def run_gpu(args):
     clocks = sampler.stop()
     ctx.sync()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    t_ms = float(np.mean(step_ms))
-    if dist is not None:
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
-        dist.barrier()
+    t_ms = max_over_ranks(float(np.mean(step_ms)), dist, dev)
     cells = M * N
     value = ws * cells / (t_ms * 1e-3) / 1e9
 
@@ -233,11 +239,7 @@ def run_gpu(args):
         dt = time.perf_counter() - t0
         if k >= args.warmup:
             e2e_times.append(dt)
-    e2e_s = float(np.mean(e2e_times)) if e2e_times else float("nan")
-    if dist is not None:
-        tt = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = max_over_ranks(float(np.mean(e2e_times)) if e2e_times else float("nan"), dist, dev)
     assert args.no_e2e or len(s_out) == L
 
     # roofline of the dominant kernel (the fill): algorithmic bytes = the 1-bit-per-cell direction bitmap
