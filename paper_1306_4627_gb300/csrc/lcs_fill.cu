@@ -124,6 +124,8 @@ struct Warp {
 struct Lane {
   uint32_t V;         // the lane's word of the current row vector
   uint32_t cout;      // carry bits produced in the last step (row 0 of the block at bit 31)
+  uint32_t cin_a;     // carries for rows 0 .. B/2-1 of this step from lane-1 (top bits), received last step
+  uint32_t cin_b;     // carries for rows B/2 .. B-1
   uint32_t win;       // inbound window of the current 32-step block t0 .. t0+31: slot t0 + lane
   uint32_t win_next;  // the next block's window, requested in the middle of the current block
   uint32_t cap;       // V captured at the end of this lane's row-block r with (r + 1) % 32 == 0 in this block
@@ -132,52 +134,38 @@ struct Lane {
   bool failed;
 };
 
-// The B rows of one step, given the match masks P of the rows. KT selects the row form: 0 = U = V & P;
-// S = V + U + c; V' = S | (V & ~P) (three dependent operations per row); 1 = the same values with V & ~P carried
-// from the previous row, so that V' and the next row's U come from S in one operation each.
-template <int B, bool TB, int KT>
-__device__ __forceinline__ void rows(const uint32_t (&P)[B], uint32_t& V, uint32_t cin, uint32_t& co,
-                                     uint32_t (&tw)[B]) {
-  uint32_t cw = cin;
+// One row of the update: U = V & P; S = V + U + (carry bit at the top of cw); V' = S | (V & ~P); the carry out of
+// the word is shifted into co; T (the carries into every bit) is kept in traceback mode.
+template <bool TB>
+__device__ __forceinline__ void row1(uint32_t P, uint32_t& V, uint32_t& cw, uint32_t& co, uint32_t& tw) {
+  const uint32_t U = V & P;
+  uint32_t S;
+  asm("add.cc.u32 %0, %0, %0;\n\t"
+      "addc.cc.u32 %1, %3, %4;\n\t"
+      "addc.u32 %2, %2, %2;"
+      : "+r"(cw), "=r"(S), "+r"(co)
+      : "r"(V), "r"(U));
+  if (TB) tw = S ^ V ^ U;
+  V = S | (V & ~P);
+}
+
+// The B rows of one step. The carries entering the word come in two halves (rows 0 .. B/2-1 in cin_a, the rest in
+// cin_b, each at the top bits); the carries leaving it go to lane+1 in two halves as well, the first right after
+// row B/2-1, so that lane+1 has them long before its next step needs them and no shuffle latency sits on the chain
+// of rows. Returns the full B carry-out bits (row 0 at bit B-1) in co.
+template <int B, bool TB>
+__device__ __forceinline__ void rows(const uint32_t (&P)[B], uint32_t& V, uint32_t cin_a, uint32_t cin_b,
+                                     uint32_t& co, uint32_t& send_a, uint32_t& send_b, uint32_t (&tw)[B]) {
+  constexpr int H = B / 2;
+  uint32_t cw = cin_a;
   co = 0;
-  if (KT == 0) {
 #pragma unroll
-    for (int b = 0; b < B; ++b) {
-      const uint32_t U = V & P[b];
-      uint32_t S;
-      asm("add.cc.u32 %0, %0, %0;\n\t"
-          "addc.cc.u32 %1, %3, %4;\n\t"
-          "addc.u32 %2, %2, %2;"
-          : "+r"(cw), "=r"(S), "+r"(co)
-          : "r"(V), "r"(U));
-      if (TB) tw[b] = S ^ V ^ U;
-      V = S | (V & ~P[b]);
-    }
-  } else {
-    uint32_t U = V & P[0], N = V & ~P[0];
+  for (int b = 0; b < H; ++b) row1<TB>(P[b], V, cw, co, tw[b]);
+  send_a = __shfl_up_sync(kFull, co << (32 - H), 1);
+  cw = cin_b;
 #pragma unroll
-    for (int b = 0; b < B; ++b) {
-      uint32_t S;
-      asm("add.cc.u32 %0, %0, %0;\n\t"
-          "addc.cc.u32 %1, %3, %4;\n\t"
-          "addc.u32 %2, %2, %2;"
-          : "+r"(cw), "=r"(S), "+r"(co)
-          : "r"(V), "r"(U));
-      if (TB) tw[b] = S ^ V ^ U;
-      if (b + 1 < B) {
-        // V' = S | N, U' = (S | N) & P', N' = (S | N) & ~P', each one LOP3 straight from S
-        const uint32_t Pn = P[b + 1 < B ? b + 1 : b];
-        uint32_t Un, Nn;
-        asm("lop3.b32 %0, %1, %2, %3, 0xA8;" : "=r"(Un) : "r"(S), "r"(N), "r"(Pn));
-        asm("lop3.b32 %0, %1, %2, %3, 0x54;" : "=r"(Nn) : "r"(S), "r"(N), "r"(Pn));
-        V = S | N;
-        U = Un;
-        N = Nn;
-      } else {
-        V = S | N;
-      }
-    }
-  }
+  for (int b = H; b < B; ++b) row1<TB>(P[b], V, cw, co, tw[b]);
+  send_b = __shfl_up_sync(kFull, co << (32 - H), 1);
 }
 
 // Symbol offsets of row-block rb from the warp's shared ring (B words). The ring is laid out [B/4][64] in 16-byte
@@ -215,16 +203,17 @@ __device__ __forceinline__ void fill_step(const Warp& w, Lane& s, int32_t t, con
   const int32_t r = t - (int32_t)lane;
   p_from_offsets<B>(w, xa, pl);
   xo_from_ring<B>(w, r + 2, xl);
-  const uint32_t c_up = __shfl_up_sync(kFull, s.cout, 1);
   uint32_t cin0 = 0;
   if (SRC != kSrcNone) {
     const uint32_t src = __shfl_sync(kFull, s.win, t & 31);
     cin0 = t < w.R ? (src & ~kTagMask) : 0u;
   }
-  const uint32_t cin = lane == 0 ? cin0 : c_up;
+  // lane 0 takes the previous warp's carries (rows 0 .. B/2-1 at the top of cin0, then the rest)
+  const uint32_t cin_a = lane == 0 ? cin0 : s.cin_a;
+  const uint32_t cin_b = lane == 0 ? (cin0 << (B / 2)) : s.cin_b;
   uint32_t co, V = s.V;
   uint32_t tw[B];
-  rows<B, TB, KT>(pu, V, cin, co, tw);
+  rows<B, TB>(pu, V, cin_a, cin_b, co, s.cin_a, s.cin_b, tw);
   s.V = V;
   s.cout = co << (32 - B);
   if (TB) {
@@ -435,6 +424,8 @@ __global__ void __launch_bounds__(kFillThreads, 1) k_fill(const __grid_constant_
   Lane s;
   s.V = kFull;
   s.cout = 0;
+  s.cin_a = 0;
+  s.cin_b = 0;
   s.failed = false;
   s.cap = 0;
   w.snap = J.snap ? J.snap + gw * 32 + lane : nullptr;
