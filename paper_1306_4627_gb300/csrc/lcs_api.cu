@@ -72,7 +72,7 @@ int take_status(lcs_ctx* c) {
 
 // Runs one or two fill jobs: one cooperative launch when all their blocks fit on the GPU at once, otherwise each
 // job alone, in passes of at most max_coop blocks (the carry slots between passes are complete in memory).
-int run_fill(lcs_ctx* c, FillJob* jobs, int njobs, bool traceback, cudaStream_t st) {
+int run_fill(lcs_ctx* c, FillJob* jobs, int njobs, bool traceback, uint32_t B, cudaStream_t st) {
   FillArgs a{};
   a.status = c->status();
   a.spin_limit = c->spin_limit;
@@ -87,7 +87,7 @@ int run_fill(lcs_ctx* c, FillJob* jobs, int njobs, bool traceback, cudaStream_t 
       a.job[k].nblocks = jobs[k].nblocks_total;
     }
     a.njobs = (uint32_t)njobs;
-    return from_cuda(launch_fill(a, c->fill_B, traceback, st));
+    return from_cuda(launch_fill(a, B, traceback, st));
   }
   for (int k = 0; k < njobs; ++k) {
     for (uint32_t b0 = 0; b0 < jobs[k].nblocks_total; b0 += (uint32_t)c->max_coop) {
@@ -95,7 +95,7 @@ int run_fill(lcs_ctx* c, FillJob* jobs, int njobs, bool traceback, cudaStream_t 
       a.job[0].block0 = b0;
       a.job[0].nblocks = std::min<uint32_t>((uint32_t)c->max_coop, jobs[k].nblocks_total - b0);
       a.njobs = 1;
-      int rc = from_cuda(launch_fill(a, c->fill_B, traceback, st));
+      int rc = from_cuda(launch_fill(a, B, traceback, st));
       if (rc) return rc;
     }
   }
@@ -177,7 +177,7 @@ int run_length(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, u
     jobs[1].R = Rr;
   }
   c->mark(1, st);
-  rc = run_fill(c, jobs, split ? 2 : 1, false, st);
+  rc = run_fill(c, jobs, split ? 2 : 1, false, B, st);
   c->mark(2, st);
   if (rc) return rc;
   if (split)
@@ -196,7 +196,7 @@ int run_length(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, u
 int run_traceback(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, uint64_t n, uint8_t* d_out,
                   uint64_t out_cap, uint64_t* d_out_len, cudaStream_t st) {
   if (m == 0 || n == 0) return from_cuda(cudaMemsetAsync(d_out_len, 0, sizeof(uint64_t), st));
-  const uint32_t B = c->fill_B;
+  const uint32_t B = c->fill_B_tb;
   const Geo g = geo_for(n);
   // Segments of H rows for the parallel walk, at most kMaxSegments of them. H is a multiple of 32 * B: the fill
   // kernel snapshots a lane's word once per 32 steps.
@@ -260,7 +260,7 @@ int run_traceback(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y
     jobs[1].R = Rr;
   }
   c->mark(1, st);
-  rc = run_fill(c, jobs, rev ? 2 : 1, true, st);
+  rc = run_fill(c, jobs, rev ? 2 : 1, true, B, st);
   c->mark(2, st);
   if (rc) return rc;
   TraceArgs t{};
@@ -326,7 +326,7 @@ extern "C" int lcs_ctx_create(int device, lcs_ctx** out) {
     lcs_ctx_destroy(c);
     return rc;
   }
-  if (const char* e = getenv("LCS_FILL_B")) c->fill_B = (atoi(e) == 16) ? 16u : 8u;
+  if (const char* e = getenv("LCS_FILL_B")) c->fill_B = c->fill_B_tb = (atoi(e) == 16) ? 16u : 8u;
   if (const char* e = getenv("LCS_FILL_VARIANT")) c->fill_variant = (uint32_t)atoi(e);
   // bounded-wait testing: a short wait limit and a carry hand-off that is never published
   if (const char* e = getenv("LCS_SPIN_LIMIT")) c->spin_limit = (uint32_t)std::max(64, atoi(e));

@@ -195,7 +195,7 @@ __device__ __forceinline__ void p_from_offsets(const Warp& w, const uint32_t (&x
 // already holds) and the offsets of the step after that, so no step waits on a load. Lane 0 takes the previous
 // warp's carries from the block's window (validated once per block), lane 31 hands its own on; the step has no
 // branches.
-template <int B, bool TB, int KT, bool SNAP, int SRC, int DST>
+template <int B, bool TB, bool SNAP, int SRC, int DST>
 __device__ __forceinline__ void fill_step(const Warp& w, Lane& s, int32_t t, const uint32_t (&pu)[B],
                                           const uint32_t (&xa)[B], uint32_t (&pl)[B], uint32_t (&xl)[B]) {
   constexpr uint32_t kTagMask = (1u << (32 - B)) - 1u;
@@ -278,11 +278,44 @@ __device__ __forceinline__ uint32_t window_load(const Warp& w, int32_t q) {
   return lds_vol_u32(w.ring_src + ((uint32_t)q & (kRing - 1)) * 4u);
 }
 
-// Start of the 32-step block t0: switch to the window requested in the middle of the last block and make sure
-// every slot this block needs has arrived (all lanes together; a bounded wait in the rare case one has not).
+// Start of a VG-step group at t (t % VG == 0) for a warp fed by a shared-memory ring: lanes t%32 .. t%32+VG-1 of
+// the window load the group's VG slots and the warp waits until all of them have arrived (bounded). A group only
+// needs the producer VG + 31 steps ahead, so neighbouring warps in a block run close together.
+template <int B, int SRC, int VG>
+__device__ __forceinline__ void ring_group_validate(const Warp& w, Lane& s, int32_t t) {
+  if (SRC != kSrcRing) return;
+  constexpr uint32_t kTagMask = (1u << (32 - B)) - 1u;
+  constexpr uint32_t kSel = 32u - VG;  // lane bits that select the group
+  const uint32_t lane = w.lane;
+  const bool mine = (lane & kSel) == ((uint32_t)t & kSel);
+  const int32_t q = (t & ~31) + (int32_t)lane;
+  const uint32_t want = ((uint32_t)(q + 1) | 1u) & kTagMask;
+  if (mine) s.win = q < w.R ? lds_vol_u32(w.ring_src + ((uint32_t)q & (kRing - 1)) * 4u) : 0u;
+  bool ok = !mine || q >= w.R || (s.win & kTagMask) == want;
+  if (__all_sync(kFull, ok) || s.failed) return;
+  for (uint32_t it = 0;; ++it) {
+    if (!ok) {
+      s.win = lds_vol_u32(w.ring_src + ((uint32_t)q & (kRing - 1)) * 4u);
+      ok = (s.win & kTagMask) == want;
+    }
+    if (__all_sync(kFull, ok)) return;
+    if ((it & 63u) == 63u) {
+      const bool quit = __any_sync(kFull, give_up(w.status, it, w.spin_limit, 2u));
+      if (quit) {
+        s.failed = true;
+        return;
+      }
+    }
+    __nanosleep(32);
+  }
+}
+
+// Start of the 32-step block t0 for a warp fed by global slots: switch to the window requested in the middle of the
+// last block and make sure every slot this block needs has arrived (all lanes together; a bounded wait in the rare
+// case one has not).
 template <int B, int SRC>
 __device__ __forceinline__ void window_validate(const Warp& w, Lane& s, int32_t t0, bool first) {
-  if (SRC == kSrcNone) return;
+  if (SRC != kSrcGlobal) return;
   constexpr uint32_t kTagMask = (1u << (32 - B)) - 1u;
   if (!first) s.win = s.win_next;
   const int32_t q = t0 + (int32_t)w.lane;
@@ -318,7 +351,7 @@ __device__ __forceinline__ void block_start(const Warp& w, Lane& s, int32_t t) {
   }
 }
 
-template <int B, bool TB, int KT, bool SNAP, int SRC, int DST>
+template <int B, bool TB, int VG, bool SNAP, int SRC, int DST>
 __device__ __forceinline__ void warp_loop(const Warp& w, Lane& s) {
   const int32_t lane = (int32_t)w.lane;
   uint32_t x0[B], x1[B], p0[B], p1[B];
@@ -330,7 +363,7 @@ __device__ __forceinline__ void warp_loop(const Warp& w, Lane& s) {
   xo_load_global<B>(w, 1 - lane, x1);  // step 1's row-block
   __syncwarp();
   p_from_offsets<B>(w, x0, p0);
-  if (SRC != kSrcNone) s.win = window_load<SRC>(w, lane);
+  if (SRC == kSrcGlobal) s.win = window_load<SRC>(w, lane);
   const int32_t steps = w.R + 31;
   int32_t t = 0;
   // pipeline at an even step t: p0 = masks of step t, x1 = offsets of step t+1
@@ -339,15 +372,14 @@ __device__ __forceinline__ void warp_loop(const Warp& w, Lane& s) {
     window_validate<B, SRC>(w, s, t, t == 0);
     block_start<SRC, DST>(w, s, t);
 #pragma unroll 1
-    for (int k = 0; k < 16; k += 2) {
-      fill_step<B, TB, KT, SNAP, SRC, DST>(w, s, t + k, p0, x1, p1, x0);
-      fill_step<B, TB, KT, SNAP, SRC, DST>(w, s, t + k + 1, p1, x0, p0, x1);
-    }
-    if (SRC != kSrcNone) s.win_next = window_load<SRC>(w, t + 32 + lane);  // the next block's window
+    for (int g = 0; g < 32 / VG; ++g) {
+      ring_group_validate<B, SRC, VG>(w, s, t + VG * g);
 #pragma unroll 1
-    for (int k = 16; k < 32; k += 2) {
-      fill_step<B, TB, KT, SNAP, SRC, DST>(w, s, t + k, p0, x1, p1, x0);
-      fill_step<B, TB, KT, SNAP, SRC, DST>(w, s, t + k + 1, p1, x0, p0, x1);
+      for (int k = VG * g; k < VG * g + VG; k += 2) {
+        fill_step<B, TB, SNAP, SRC, DST>(w, s, t + k, p0, x1, p1, x0);
+        fill_step<B, TB, SNAP, SRC, DST>(w, s, t + k + 1, p1, x0, p0, x1);
+      }
+      if (SRC == kSrcGlobal && VG * g + VG == 16) s.win_next = window_load<SRC>(w, t + 32 + lane);  // next window
     }
     if (SNAP) snap_store(w, s, t, steps);
   }
@@ -356,23 +388,27 @@ __device__ __forceinline__ void warp_loop(const Warp& w, Lane& s) {
   block_start<SRC, DST>(w, s, t);
   const int32_t t_tail = t;
   for (; t + 1 < steps; t += 2) {
-    fill_step<B, TB, KT, SNAP, SRC, DST>(w, s, t, p0, x1, p1, x0);
-    fill_step<B, TB, KT, SNAP, SRC, DST>(w, s, t + 1, p1, x0, p0, x1);
+    if ((t & (VG - 1)) == 0) ring_group_validate<B, SRC, VG>(w, s, t);
+    fill_step<B, TB, SNAP, SRC, DST>(w, s, t, p0, x1, p1, x0);
+    fill_step<B, TB, SNAP, SRC, DST>(w, s, t + 1, p1, x0, p0, x1);
   }
-  if (t < steps) fill_step<B, TB, KT, SNAP, SRC, DST>(w, s, t, p0, x1, p1, x0);
+  if (t < steps) {
+    if ((t & (VG - 1)) == 0) ring_group_validate<B, SRC, VG>(w, s, t);
+    fill_step<B, TB, SNAP, SRC, DST>(w, s, t, p0, x1, p1, x0);
+  }
   if (SNAP) snap_store(w, s, t_tail, steps);
 }
 
-template <int B, bool TB, int KT, bool SNAP>
+template <int B, bool TB, int VG, bool SNAP>
 __device__ __forceinline__ void dispatch(const Warp& w, Lane& s, bool first_warp, bool last_warp, uint32_t wib) {
-  if (first_warp) warp_loop<B, TB, KT, SNAP, kSrcNone, kDstRing>(w, s);
-  else if (wib == 0) warp_loop<B, TB, KT, SNAP, kSrcGlobal, kDstRing>(w, s);
-  else if (wib + 1 < kFillWarps) warp_loop<B, TB, KT, SNAP, kSrcRing, kDstRing>(w, s);
-  else if (!last_warp) warp_loop<B, TB, KT, SNAP, kSrcRing, kDstGlobal>(w, s);
-  else warp_loop<B, TB, KT, SNAP, kSrcRing, kDstNone>(w, s);
+  if (first_warp) warp_loop<B, TB, VG, SNAP, kSrcNone, kDstRing>(w, s);
+  else if (wib == 0) warp_loop<B, TB, VG, SNAP, kSrcGlobal, kDstRing>(w, s);
+  else if (wib + 1 < kFillWarps) warp_loop<B, TB, VG, SNAP, kSrcRing, kDstRing>(w, s);
+  else if (!last_warp) warp_loop<B, TB, VG, SNAP, kSrcRing, kDstGlobal>(w, s);
+  else warp_loop<B, TB, VG, SNAP, kSrcRing, kDstNone>(w, s);
 }
 
-template <int B, bool TB, int KT>
+template <int B, bool TB, int VG>
 __global__ void __launch_bounds__(kFillThreads, 1) k_fill(const __grid_constant__ FillArgs a) {
   static_assert(B % 4 == 0 && B >= 4 && B <= 16, "row-block height");
   extern __shared__ __align__(16) uint32_t sm[];
@@ -436,11 +472,11 @@ __global__ void __launch_bounds__(kFillThreads, 1) k_fill(const __grid_constant_
   s.tp = J.T ? reinterpret_cast<uint4*>(J.T + (gw * (J.R + 31)) * 32 * (uint64_t)B) + lane : nullptr;
 
   if (TB && J.T) {
-    dispatch<B, true, KT, true>(w, s, first_warp, last_warp, wib);
+    dispatch<B, true, VG, true>(w, s, first_warp, last_warp, wib);
   } else if (TB && J.snap) {  // the table of the reversed strings in a traceback launch: snapshots, no bitmap
-    dispatch<B, false, KT, true>(w, s, first_warp, last_warp, wib);
+    dispatch<B, false, VG, true>(w, s, first_warp, last_warp, wib);
   } else {
-    dispatch<B, false, KT, false>(w, s, first_warp, last_warp, wib);
+    dispatch<B, false, VG, false>(w, s, first_warp, last_warp, wib);
   }
 
   if (J.final_v) J.final_v[gw * 32 + lane] = s.V;
@@ -450,9 +486,9 @@ __global__ void __launch_bounds__(kFillThreads, 1) k_fill(const __grid_constant_
   }
 }
 
-template <int B, bool TB, int KT>
+template <int B, bool TB, int VG>
 cudaError_t launch_t(const FillArgs& a, cudaStream_t st) {
-  auto fn = k_fill<B, TB, KT>;
+  auto fn = k_fill<B, TB, VG>;
   const size_t smem = fill_smem_bytes();
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -471,24 +507,26 @@ size_t fill_smem_bytes() {
 int fill_max_coop_blocks(int device) {
   int sms = 0, per_sm = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
-  auto fn = k_fill<8, true, 0>;
+  auto fn = k_fill<8, true, 16>;
   const size_t smem = fill_smem_bytes();
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kFillThreads, smem) != cudaSuccess) return 0;
   return sms * per_sm;
 }
 
-// variant: bit 0 = shorter row chain (KT); B = rows per step (8 or 16)
+// B = rows per step (8 or 16); variant bits 1-2 choose the hand-off validation group of ring-fed warps: 0 = the
+// default (16 steps for B = 8, 8 for B = 16), otherwise 1 = the smaller (8 / 8), 2 = the larger (32 / 16). All
+// give the same results; only the pipeline lag and the per-step overhead differ.
+template <int B, int VGD, int VGA>
+cudaError_t launch_b(const FillArgs& a, bool traceback, cudaStream_t st) {
+  const int sel = (a.variant >> 1) & 3;
+  if (sel == 2) return traceback ? launch_t<B, true, VGA>(a, st) : launch_t<B, false, VGA>(a, st);
+  return traceback ? launch_t<B, true, VGD>(a, st) : launch_t<B, false, VGD>(a, st);
+}
+
 cudaError_t launch_fill(const FillArgs& a, uint32_t B, bool traceback, cudaStream_t st) {
-  const int kt = (a.variant & 1) ? 1 : 0;
-  if (B == 8) {
-    if (traceback) return kt ? launch_t<8, true, 1>(a, st) : launch_t<8, true, 0>(a, st);
-    return kt ? launch_t<8, false, 1>(a, st) : launch_t<8, false, 0>(a, st);
-  }
-  if (B == 16) {
-    if (traceback) return kt ? launch_t<16, true, 1>(a, st) : launch_t<16, true, 0>(a, st);
-    return kt ? launch_t<16, false, 1>(a, st) : launch_t<16, false, 0>(a, st);
-  }
+  if (B == 8) return launch_b<8, 16, 32>(a, traceback, st);
+  if (B == 16) return launch_b<16, 8, 16>(a, traceback, st);
   return cudaErrorInvalidValue;
 }
 
