@@ -379,10 +379,11 @@ extern "C" int lcs_ctx_last_profile(lcs_ctx* c, lcs_profile* out) {
   int rc = from_cuda(cudaEventSynchronize(c->ev[3]));
   if (rc) return rc;
   float t01 = 0, t12 = 0, t23 = 0, t03 = 0;
-  cudaEventElapsedTime(&t01, c->ev[0], c->ev[1]);
-  cudaEventElapsedTime(&t12, c->ev[1], c->ev[2]);
-  cudaEventElapsedTime(&t23, c->ev[2], c->ev[3]);
-  cudaEventElapsedTime(&t03, c->ev[0], c->ev[3]);
+  rc = from_cuda(cudaEventElapsedTime(&t01, c->ev[0], c->ev[1]));
+  if (!rc) rc = from_cuda(cudaEventElapsedTime(&t12, c->ev[1], c->ev[2]));
+  if (!rc) rc = from_cuda(cudaEventElapsedTime(&t23, c->ev[2], c->ev[3]));
+  if (!rc) rc = from_cuda(cudaEventElapsedTime(&t03, c->ev[0], c->ev[3]));
+  if (rc) return rc;
   out->prep_ms = t01;
   out->fill_ms = t12;
   out->trace_ms = c->prof_trace ? t23 : 0.0;

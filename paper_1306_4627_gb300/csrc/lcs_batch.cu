@@ -166,32 +166,44 @@ __global__ void __launch_bounds__(kBatchWarps * 32) k_batch_main(BatchArgs a) {
     const uint32_t zero_code = sig;  // the all-zero row of this pair
     uint32_t V[kBK] = {kFull, kFull, kFull, kFull};
     const uint32_t rows = item.rows;
-    uint32_t code_next = (has && 0 < pr.m) ? xc[0] : zero_code;
-    for (uint32_t i = 0; i < rows; ++i) {
-      const uint32_t code = code_next;
-      code_next = (has && i + 1 < pr.m) ? xc[i + 1] : zero_code;
-      uint32_t P[kBK];
-      if (staged) {
-        const uint4 q = *reinterpret_cast<const uint4*>(&stage[code * kWarpWords + lane * kBK]);
-        P[0] = q.x; P[1] = q.y; P[2] = q.z; P[3] = q.w;
-      } else {
+    // symbol codes are requested 8 rows before they are used (the rows beyond a pair's m read its zero row)
+    auto codes8 = [&](uint32_t i0, uint32_t (&c)[8]) {
 #pragma unroll
-        for (int k = 0; k < kBK; ++k) {
-          const uint32_t q = w0 + k;
-          P[k] = (has && q < pr.w) ? __ldg(a.peq + pr.peq_off + (uint64_t)code * pr.w + q) : 0u;
+      for (int b = 0; b < 8; ++b) c[b] = (has && i0 + b < pr.m) ? (uint32_t)__ldg(xc + i0 + b) : zero_code;
+    };
+    uint32_t cq[8], nq[8];
+    codes8(0, cq);
+    for (uint32_t i0 = 0; i0 < rows; i0 += 8) {
+      codes8(i0 + 8, nq);
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        if (i0 + b >= rows) break;  // warp-uniform
+        const uint32_t code = cq[b];
+        uint32_t P[kBK];
+        if (staged) {
+          const uint4 q = *reinterpret_cast<const uint4*>(&stage[code * kWarpWords + lane * kBK]);
+          P[0] = q.x; P[1] = q.y; P[2] = q.z; P[3] = q.w;
+        } else {
+#pragma unroll
+          for (int k = 0; k < kBK; ++k) {
+            const uint32_t q = w0 + k;
+            P[k] = (has && q < pr.w) ? __ldg(a.peq + pr.peq_off + (uint64_t)code * pr.w + q) : 0u;
+          }
         }
+        uint32_t U[kBK], S[kBK], gen;
+#pragma unroll
+        for (int k = 0; k < kBK; ++k) U[k] = V[k] & P[k];
+        add4(V, U, S, gen);
+        const uint32_t prop = (S[0] & S[1] & S[2] & S[3]) == kFull;
+        const uint32_t Gb = __ballot_sync(kFull, gen), Pb = __ballot_sync(kFull, prop);
+        const uint32_t A = (Gb | Pb) & ~top, Bv = Gb & ~top;
+        const uint32_t cin = (((A + Bv) ^ A ^ Bv) >> lane) & 1u;
+        inc4(S, cin);
+#pragma unroll
+        for (int k = 0; k < kBK; ++k) V[k] = S[k] | (V[k] & ~P[k]);
       }
-      uint32_t U[kBK], S[kBK], gen;
 #pragma unroll
-      for (int k = 0; k < kBK; ++k) U[k] = V[k] & P[k];
-      add4(V, U, S, gen);
-      const uint32_t prop = (S[0] & S[1] & S[2] & S[3]) == kFull;
-      const uint32_t Gb = __ballot_sync(kFull, gen), Pb = __ballot_sync(kFull, prop);
-      const uint32_t A = (Gb | Pb) & ~top, Bv = Gb & ~top;
-      const uint32_t cin = (((A + Bv) ^ A ^ Bv) >> lane) & 1u;
-      inc4(S, cin);
-#pragma unroll
-      for (int k = 0; k < kBK; ++k) V[k] = S[k] | (V[k] & ~P[k]);
+      for (int b = 0; b < 8; ++b) cq[b] = nq[b];
     }
     // c[m, n] = zero bits of V over the pair's n columns (bits past n stay 1), summed over the group's lanes
     uint32_t z = 0;
@@ -274,68 +286,125 @@ namespace lcs {
 int run_length(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, uint64_t n, uint64_t* d_out,
                cudaStream_t st);
 
-// Runs a planned batch whose xs / ys / out_lens are already on the device.
-int run_batch(lcs_ctx* c, const uint8_t* d_xs, const uint8_t* d_ys, const uint64_t* x_off, const uint64_t* y_off,
-              uint64_t count, uint64_t* d_out, cudaStream_t st) {
-  Plan plan;
-  std::vector<uint64_t> big;
-  make_plan(x_off, y_off, count, plan, big);
-  uint64_t cells = 0;
-  for (uint64_t k = 0; k < count; ++k) cells += (x_off[k + 1] - x_off[k]) * (y_off[k + 1] - y_off[k]);
-  c->mark(0, st);
-  int rc = from_cuda(cudaMemsetAsync(d_out, 0, count * sizeof(uint64_t), st));  // empty pairs: length 0
-  if (rc) return rc;
-  if (!plan.pairs.empty()) {
-    const size_t pb = plan.pairs.size() * sizeof(BPair), ib = plan.items.size() * sizeof(BItem);
-    rc = from_cuda(ensure(c->bplan, pb + ib + 256));
-    if (!rc) rc = from_cuda(ensure(c->bsig, plan.pairs.size() * 4 + 4));
-    if (!rc) rc = from_cuda(ensure(c->bxcode, std::max<uint64_t>(x_off[count] - x_off[0], 1)));
-    if (!rc) rc = from_cuda(ensure(c->bpeq, plan.peq_words * 4 + 4));
-    if (rc) return rc;
-    // (copies from pageable memory: the runtime has staged the data when the call returns)
-    rc = from_cuda(cudaMemcpyAsync(c->bplan.p, plan.pairs.data(), pb, cudaMemcpyHostToDevice, st));
-    if (!rc) rc = from_cuda(cudaMemcpyAsync((char*)c->bplan.p + pb, plan.items.data(), ib, cudaMemcpyHostToDevice, st));
-    if (!rc) rc = from_cuda(cudaMemsetAsync((char*)c->small.p + kOffTicket, 0, 4, st));
-    if (rc) return rc;
-    BatchArgs a{};
-    a.xs = d_xs;
-    a.ys = d_ys;
-    a.pairs = (const BPair*)c->bplan.p;
-    a.items = (const BItem*)((char*)c->bplan.p + pb);
-    a.sigma = (uint32_t*)c->bsig.p;
-    a.xcode = (uint8_t*)c->bxcode.p;
-    a.peq = (uint32_t*)c->bpeq.p;
-    a.out_lens = d_out;
-    a.ticket = (uint32_t*)((char*)c->small.p + kOffTicket);
-    a.npairs = (uint32_t)plan.pairs.size();
-    a.nitems = (uint32_t)plan.items.size();
-    int sms = 0;
+static uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
+  const unsigned char* b = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+  return h;
+}
+
+// The launches of a planned batch: zero the outputs, per-pair prep, the persistent kernel (stage events around
+// them when profiling).
+static void batch_launches(lcs_ctx* c, uint64_t* d_out, uint64_t count, const BatchArgs& a, cudaStream_t st,
+                           bool marks) {
+  if (marks) c->mark(0, st);
+  cudaMemsetAsync(d_out, 0, count * sizeof(uint64_t), st);  // empty pairs: length 0
+  if (a.npairs) {
+    cudaMemsetAsync(a.ticket, 0, 4, st);
+    int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-    const unsigned prep_blocks = (unsigned)std::min<uint64_t>((plan.pairs.size() + 7) / 8, (uint64_t)sms * 8);
+    const unsigned prep_blocks = (unsigned)std::min<uint64_t>((a.npairs + 7) / 8, (uint64_t)sms * 8);
     k_batch_prep<<<prep_blocks, 256, 0, st>>>(a);
-    int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_main, kBatchWarps * 32, 0);
     const unsigned blocks = (unsigned)std::max(1, sms * std::max(per_sm, 1));
-    c->mark(1, st);
+    if (marks) c->mark(1, st);
     k_batch_main<<<blocks, kBatchWarps * 32, 0, st>>>(a);
-    c->mark(2, st);
-    c->prof_blocks = blocks;
-    rc = from_cuda(cudaGetLastError());
-    if (rc) return rc;
-  } else {
+    if (marks) c->mark(2, st);
+    c->bblocks = blocks;
+  } else if (marks) {
     c->mark(1, st);
     c->mark(2, st);
   }
+}
+
+// Runs a batch whose xs / ys / out_lens are already on the device. The first call of a batch plans it on the host
+// and uploads the plan; a later call with the same pairs (same offsets and buffers) reuses it. Without profiling
+// the launches are captured once as a CUDA graph and replayed.
+int run_batch(lcs_ctx* c, const uint8_t* d_xs, const uint8_t* d_ys, const uint64_t* x_off, const uint64_t* y_off,
+              uint64_t count, uint64_t* d_out, cudaStream_t st) {
+  uint64_t key = 1469598103934665603ull;
+  const uint64_t ptrs[4] = {count, (uint64_t)d_xs, (uint64_t)d_ys, (uint64_t)d_out};
+  key = fnv1a(key, ptrs, sizeof(ptrs));
+  for (uint64_t k = 0; k <= count; ++k) {
+    const uint64_t rel[2] = {x_off[k] - x_off[0], y_off[k] - y_off[0]};
+    key = fnv1a(key, rel, sizeof(rel));
+  }
+  int rc = LCS_OK;
+  if (key != c->bkey) {
+    if (c->bexec) cudaGraphExecDestroy(c->bexec);
+    c->bexec = nullptr;
+    c->bkey = 0;
+    Plan plan;
+    c->bbig.clear();
+    make_plan(x_off, y_off, count, plan, c->bbig);
+    c->bcells = 0;
+    for (uint64_t k = 0; k < count; ++k) c->bcells += (x_off[k + 1] - x_off[k]) * (y_off[k + 1] - y_off[k]);
+    const size_t pb = plan.pairs.size() * sizeof(BPair), ib = plan.items.size() * sizeof(BItem);
+    if (!plan.pairs.empty()) {
+      rc = from_cuda(ensure(c->bplan, pb + ib + 256));
+      if (!rc) rc = from_cuda(ensure(c->bsig, plan.pairs.size() * 4 + 4));
+      if (!rc) rc = from_cuda(ensure(c->bxcode, std::max<uint64_t>(x_off[count] - x_off[0], 1)));
+      if (!rc) rc = from_cuda(ensure(c->bpeq, plan.peq_words * 4 + 4));
+      if (rc) return rc;
+      // (copies from pageable memory: the runtime has staged the data when the call returns)
+      rc = from_cuda(cudaMemcpyAsync(c->bplan.p, plan.pairs.data(), pb, cudaMemcpyHostToDevice, st));
+      if (!rc) rc = from_cuda(cudaMemcpyAsync((char*)c->bplan.p + pb, plan.items.data(), ib, cudaMemcpyHostToDevice, st));
+      if (rc) return rc;
+    }
+    c->bnpairs = plan.pairs.size();
+    c->bnitems = plan.items.size();
+    c->bpairs_bytes = pb;
+    c->bkey = key;
+  }
+  BatchArgs a{};
+  a.xs = d_xs;
+  a.ys = d_ys;
+  a.pairs = (const BPair*)c->bplan.p;
+  a.items = (const BItem*)((char*)c->bplan.p + c->bpairs_bytes);
+  a.sigma = (uint32_t*)c->bsig.p;
+  a.xcode = (uint8_t*)c->bxcode.p;
+  a.peq = (uint32_t*)c->bpeq.p;
+  a.out_lens = d_out;
+  a.ticket = (uint32_t*)((char*)c->small.p + kOffTicket);
+  a.npairs = (uint32_t)c->bnpairs;
+  a.nitems = (uint32_t)c->bnitems;
+  if (c->prof) {
+    batch_launches(c, d_out, count, a, st, true);
+    rc = from_cuda(cudaGetLastError());
+  } else {
+    if (!c->bexec) {
+      if (!c->cap_stream) {
+        rc = from_cuda(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        if (rc) return rc;
+      }
+      // capture: the recorded launches do not run now; the graph runs on st below
+      rc = from_cuda(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+      if (rc) return rc;
+      batch_launches(c, d_out, count, a, c->cap_stream, false);
+      cudaGraph_t graph = nullptr;
+      rc = from_cuda(cudaStreamEndCapture(c->cap_stream, &graph));
+      if (!rc) rc = from_cuda(cudaGraphInstantiate(&c->bexec, graph, 0));
+      if (graph) cudaGraphDestroy(graph);
+      if (rc) {
+        c->bexec = nullptr;
+        return rc;
+      }
+    }
+    rc = from_cuda(cudaGraphLaunch(c->bexec, st));
+  }
+  if (rc) return rc;
   // pairs with more than 4096 columns go through the single-pair path
-  for (uint64_t k : big) {
+  for (uint64_t k : c->bbig) {
     rc = run_length(c, d_xs + (x_off[k] - x_off[0]), x_off[k + 1] - x_off[k], d_ys + (y_off[k] - y_off[0]),
                     y_off[k + 1] - y_off[k], d_out + k, st);
     if (rc) return rc;
   }
-  c->mark(3, st);
-  c->prof_valid = c->prof;
-  c->prof_trace = false;
-  c->prof_cells = cells;
+  if (c->prof) {
+    c->mark(3, st);
+    c->prof_valid = true;
+    c->prof_trace = false;
+    c->prof_cells = c->bcells;
+    c->prof_blocks = c->bblocks;
+  }
   return LCS_OK;
 }
 

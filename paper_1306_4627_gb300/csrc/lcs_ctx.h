@@ -3,6 +3,7 @@
 
 #include <cstdint>
 #include <mutex>
+#include <vector>
 
 #include "lcs_internal.h"
 
@@ -43,6 +44,12 @@ struct lcs_ctx {
   lcs::DBuf xoff_f, xoff_r, xcode, peq_f, peq_r, carry_f, carry_r, fv_f, fv_r, T, snap_f, snap_r;
   lcs::DBuf colsum, ent, ext, nch, entcnt, sel, chars;
   lcs::DBuf bplan, bsig, bxcode, bpeq, bout;  // batch: plan, per-pair alphabet sizes, codes, masks, lengths
+  // batch: the last plan's launches captured as a CUDA graph, replayed while the same batch is submitted again
+  uint64_t bkey = 0;
+  cudaGraphExec_t bexec = nullptr;
+  std::vector<uint64_t> bbig;
+  uint64_t bcells = 0, bblocks = 0, bnpairs = 0, bnitems = 0, bpairs_bytes = 0;
+  cudaStream_t cap_stream = nullptr;
   uint64_t host_word[1] = {0};
   // stage events of the last profiled call: [0] start, [1] fill start, [2] fill end, [3] end
   bool prof = false, prof_valid = false, prof_trace = false;
@@ -60,6 +67,10 @@ struct lcs_ctx {
   uint64_t* out_len() { return (uint64_t*)((char*)small.p + lcs::kOffOutLen); }
 
   void release_all() {
+    if (bexec) cudaGraphExecDestroy(bexec);
+    bexec = nullptr;
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    cap_stream = nullptr;
     lcs::DBuf* all[] = {&small, &x, &y, &out, &xoff_f, &xoff_r, &xcode, &peq_f, &peq_r, &carry_f, &carry_r,
                         &fv_f, &fv_r, &T, &snap_f, &snap_r, &colsum, &ent, &ext, &nch, &entcnt, &sel, &chars,
                         &bplan, &bsig, &bxcode, &bpeq, &bout};

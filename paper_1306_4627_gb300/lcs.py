@@ -186,6 +186,21 @@ class Context:
         _check(rc, "lcs_batch")
         return out[: len(pairs)]
 
+    def batch_concat(self, xs, x_off, ys, y_off) -> np.ndarray:
+        """lcs_batch on already concatenated host buffers with count+1 offsets each."""
+        xs, ys = _u8(xs), _u8(ys)
+        x_off = np.ascontiguousarray(x_off, dtype=np.uint64)
+        y_off = np.ascontiguousarray(y_off, dtype=np.uint64)
+        count = len(x_off) - 1
+        out = np.zeros(max(count, 1), dtype=np.uint64)
+        u64p = ctypes.POINTER(ctypes.c_uint64)
+        xs1 = xs if len(xs) else np.zeros(1, np.uint8)
+        ys1 = ys if len(ys) else np.zeros(1, np.uint8)
+        rc = _lib.lcs_batch(self._h, _p8(xs1), x_off.ctypes.data_as(u64p), _p8(ys1), y_off.ctypes.data_as(u64p), count,
+                            out.ctypes.data_as(u64p))
+        _check(rc, "lcs_batch")
+        return out[:count]
+
     # -- device buffers (torch uint8 CUDA tensors) ---------------------------------------------------------------
     def length_dev(self, x, y, out, stream=None) -> None:
         """x, y: uint8 CUDA tensors; out: a uint64/int64 CUDA tensor with at least one element."""
