@@ -1,17 +1,18 @@
 // lcs_batch: LCS lengths (c[m,n], paper §I.C) of many independent pairs in one persistent launch.
 //
 // Every pair is a small instance of the same bit-parallel row update as the single-pair fill (U = V & P;
-// S = V + U; V' = S | (V & ~P), one 32-column word per register). Here the rows of a pair are processed
-// row-synchronously by a group of G lanes of a warp, each lane holding K = 4 consecutive words of the row:
+// S = V + U; V' = S | (V & ~P), one 32-column word per register). Here the rows of a pair are processed by a group
+// of G lanes of a warp, each lane holding K = 4 consecutive words of the row:
 //   * the add inside a lane ripples through its 4 words with the carry flag;
-//   * the carries between the lanes of a group are resolved per row by a carry-lookahead over warp ballots:
-//     with g = "the lane's 128-bit add generates a carry" and p = "it would pass an incoming carry on", the
-//     carries into all lanes are ((A + B) ^ A ^ B) for A = g | p, B = g, with the groups' top lanes masked so that
-//     no carry crosses from one pair into the next;
+//   * the lanes of a group run skewed by one row each (lane g works on row t - g at step t), so the carry out of a
+//     lane's 128 bits for a row is shuffled to the next lane, which adds it in the same row one step later;
 //   * a warp works on 32 / G pairs of the same group size at once, G chosen per pair as the smallest power of two
 //     with 4 * G words >= ceil(n / 32) (so short pairs share a warp and long pairs spread over it).
 // The host plans the launch: it buckets pairs by G, orders work items (up to 32 / G pairs each) by decreasing
-// rows, and a persistent kernel lets every warp take the next item from an atomic ticket.
+// rows, and a persistent kernel lets every warp take the next item from an atomic ticket. A pair with many rows is
+// split in two jobs that run at the same time, its top half forward and its bottom half on the reversed strings;
+// a small kernel then takes L = max_j (c[mt, j] + LCS(X[mt+1..m], Y[j+1..n])) from the two final rows, so the
+// longest serial chain of rows in a batch is halved.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -34,15 +35,24 @@ constexpr int kWarpWords = 32 * kBK;  // 128 words per warp row
 constexpr int kBatchWarps = 8;     // warps per block of the persistent kernel
 constexpr int kStageRows = 24;     // match-mask rows staged in shared memory per warp (alphabets up to 23 symbols)
 
-struct BPair {        // one pair of the plan, in processing order
-  uint64_t x_off;     // first symbol of x in xs (and its codes in xcode)
+struct BPair {        // one pair of the plan
+  uint64_t x_off;     // first symbol of x in xs
   uint64_t y_off;
+  uint64_t xcf, xcr;  // codes of the forward job's rows (x[0..mt)) and of the reverse job's (x[m-1] down to x[mt])
+                      // in xcode, each list between runs of the pair's zero row index
   uint64_t peq_off;   // word offset of its match-mask table: (sigma + 1) rows of w words
+  uint64_t peqr_off;  // the table over reversed y (split pairs only)
   uint32_t m, n, w;   // rows, columns, words per row (ceil(n / 32))
   uint32_t out;       // index into out_lens
+  uint32_t mt;        // rows of the forward job (m when the pair is not split)
+  uint32_t fv;        // split pairs: final rows of the forward / reverse job in slots fv, fv + 1
 };
 
-struct BItem {        // a warp's unit of work: pairs [first, first + count) of the plan, G lanes each
+struct BJob {         // the rows of one pair a group of lanes works through
+  uint32_t pair, rev, rows, pad;
+};
+
+struct BItem {        // a warp's unit of work: jobs [first, first + count), G lanes each
   uint32_t first, count, G, rows;
 };
 
@@ -50,76 +60,219 @@ struct BatchArgs {
   const uint8_t* xs;
   const uint8_t* ys;
   const BPair* pairs;
+  const BJob* jobs;
   const BItem* items;
   uint32_t* sigma;     // per plan pair: symbols present in y (its zero row index)
-  uint8_t* xcode;      // per symbol of xs: code in its pair's alphabet
+  uint16_t* xcode;     // per job: the codes of its rows in its pair's alphabet (0..256); 16 zeros at the start
   uint32_t* peq;
+  uint32_t* fvbuf;     // final rows of split pairs' jobs, kWarpWords words per slot
   uint64_t* out_lens;
   uint32_t* ticket;
-  uint32_t npairs, nitems;
+  const uint32_t* split;  // plan indices of split pairs
+  uint32_t npairs, nitems, nsplit;
 };
 
 // ---- per-pair alphabet, symbol codes and match-mask table (one warp per pair) ------------------------------------
-__global__ void __launch_bounds__(256) k_batch_prep(BatchArgs a) {
+// Strings are read with 16-byte loads where their alignment allows (a forward job's 16-bit codes are placed so
+// that a 16-byte group of x maps to a 32-byte group of codes), and y is kept in shared memory for the alphabet
+// and the table build.
+constexpr uint32_t kMaxBatchCols = kWarpWords * 32;  // 4096: the longest y of a batch pair
+
+constexpr uint32_t kCodePadFront = 32;  // zero-row codes before a job's list: lanes run up to 31 rows behind
+constexpr uint32_t kCodePadBack = 8;    // and after it: the main kernel reads 8 rows at a time
+constexpr uint32_t kCodeZeros = 48;     // zeros at the start of xcode, read by lanes without a job (rows 0..39)
+
+// One match-mask table (see the comment in k_batch_prep): column j of the table reads y[j], or y[n - 1 - j] for
+// the table over reversed y.
+template <int NB>
+__device__ __forceinline__ void build_table(uint32_t* tab, const BPair& pr, bool reversed, const uint16_t* map,
+                                            const uint8_t* ysh, uint32_t sigma, uint32_t lane) {
+  uint32_t flip0[NB];  // for row r = lane: 0 where bit b of r is set, all ones where it is not
+#pragma unroll
+  for (int b = 0; b < NB; ++b) flip0[b] = ((lane >> b) & 1u) - 1u;
+  for (uint32_t q = 0; q < pr.w; ++q) {
+    const uint32_t j = q * 32 + lane;
+    const bool in = j < pr.n;
+    const uint32_t valid = __ballot_sync(kFull, in);
+    const uint32_t code = in ? map[ysh[reversed ? pr.n - 1 - j : j]] : 0u;
+    uint32_t pf[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) pf[b] = __ballot_sync(kFull, (code >> b) & 1u);
+    if (lane <= sigma) {
+      uint32_t mf = valid;
+#pragma unroll
+      for (int b = 0; b < NB; ++b) mf &= pf[b] ^ flip0[b];
+      tab[(uint64_t)lane * pr.w + q] = mf;
+    }
+    for (uint32_t r = lane + 32; r <= sigma; r += 32) {  // alphabets of more than 31 symbols
+      uint32_t mf = valid;
+#pragma unroll
+      for (int b = 0; b < NB; ++b) mf &= pf[b] ^ (((r >> b) & 1u) - 1u);
+      tab[(uint64_t)r * pr.w + q] = mf;
+    }
+  }
+}
+
+template <int NB>
+__device__ __noinline__ void build_tables(const BatchArgs& a, const BPair& pr, const uint16_t* map,
+                                          const uint8_t* ysh, uint32_t sigma, uint32_t lane) {
+  build_table<NB>(a.peq + pr.peq_off, pr, false, map, ysh, sigma, lane);
+  if (pr.mt < pr.m) build_table<NB>(a.peq + pr.peqr_off, pr, true, map, ysh, sigma, lane);
+}
+
+__global__ void __launch_bounds__(256, 4) k_batch_prep(BatchArgs a) {
   __shared__ uint32_t pres_s[8][8];
-  __shared__ uint8_t map_s[8][256];
+  __shared__ uint16_t map_s[8][256];
+  __shared__ __align__(16) uint8_t y_s[8][kMaxBatchCols + 16];
   const uint32_t wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t* pres = pres_s[wid];
-  uint8_t* map = map_s[wid];
+  uint16_t* map = map_s[wid];
   const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
   for (uint32_t p = blockIdx.x * (blockDim.x >> 5) + wid; p < a.npairs; p += nwarps) {
     const BPair pr = a.pairs[p];
-    if (lane < 8) pres[lane] = 0;
-    __syncwarp();
+    // y into shared memory: y[j] at ysh[j], where ysh = y_s + sh places the 16-byte groups of y on 16-byte
+    // boundaries of y_s (sh = 16 - (y mod 16), or 0 when y is aligned)
     const uint8_t* y = a.ys + pr.y_off;
-    for (uint32_t j = lane; j < pr.n; j += 32) atomicOr(&pres[y[j] >> 5], 1u << (y[j] & 31));
+    const uint32_t head = (uint32_t)((16u - ((uintptr_t)y & 15u)) & 15u);
+    const uint32_t hn = head < pr.n ? head : pr.n;
+    uint8_t* ysh = y_s[wid] + ((16u - head) & 15u);
+    const uint32_t nvec = (pr.n - hn) >> 4;
+    if (lane < hn) ysh[lane] = y[lane];
+#pragma unroll 8
+    for (uint32_t v = lane; v < nvec; v += 32)
+      *reinterpret_cast<uint4*>(ysh + hn + 16 * v) = __ldg(reinterpret_cast<const uint4*>(y + hn + 16 * v));
+    {
+      const uint32_t j = hn + 16 * nvec + lane;
+      if (lane < 16 && j < pr.n) ysh[j] = y[j];
+    }
     __syncwarp();
-    uint32_t sigma = 0;
+    // presence of each byte value: first which 32-value blocks occur, then one pass per occurring block (few for
+    // text alphabets), or one pass with a register per block when more than two blocks occur
+    {
+      if (lane < 8) pres[lane] = 0;
+      uint32_t blocks = 0;
+      for (uint32_t j = lane; j < pr.n; j += 32) blocks |= 1u << (ysh[j] >> 5);
+      blocks = __reduce_or_sync(kFull, blocks);
+      __syncwarp();
+      if (__popc(blocks) <= 2) {
+        for (uint32_t bl = blocks; bl; bl &= bl - 1) {
+          const uint32_t hi = __ffs(bl) - 1;
+          uint32_t acc = 0;
+          for (uint32_t j = lane; j < pr.n; j += 32) {
+            const uint32_t v = ysh[j];
+            acc |= (v >> 5) == hi ? 1u << (v & 31) : 0u;
+          }
+          acc = __reduce_or_sync(kFull, acc);
+          if (lane == 0) pres[hi] = acc;
+        }
+      } else {
+        uint32_t pl[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (uint32_t j = lane; j < pr.n; j += 32) {
+          const uint32_t v = ysh[j], hi = v >> 5, bit = 1u << (v & 31);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) sigma += __popc(pres[k]);
-    for (uint32_t b = lane; b < 256; b += 32) {
-      uint32_t below = 0;
-      for (uint32_t k = 0; k < (b >> 5); ++k) below += __popc(pres[k]);
-      below += __popc(pres[b >> 5] & ((1u << (b & 31)) - 1u));
-      map[b] = (uint8_t)(((pres[b >> 5] >> (b & 31)) & 1u) ? below : sigma);
+          for (uint32_t k = 0; k < 8; ++k) pl[k] |= hi == k ? bit : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const uint32_t v = __reduce_or_sync(kFull, pl[k]);
+          if (lane == (uint32_t)k) pres[k] = v;
+        }
+      }
+    }
+    __syncwarp();
+    // code of a present byte = its rank among the present bytes; absent bytes map to the zero row (sigma)
+    uint32_t sigma;
+    {
+      const uint32_t pk = lane < 8 ? pres[lane] : 0u, cnt = __popc(pk);
+      uint32_t incl = cnt;
+      for (uint32_t off = 1; off < 8; off <<= 1) {
+        const uint32_t o = __shfl_up_sync(kFull, incl, off);
+        if (lane >= off) incl += o;
+      }
+      sigma = __shfl_sync(kFull, incl, 7);
+      const uint32_t below_lane = (1u << lane) - 1u;  // lane < 32: bits under this lane's byte within a block
+#pragma unroll
+      for (uint32_t k = 0; k < 8; ++k) {
+        const uint32_t pw = __shfl_sync(kFull, pk, k), base = __shfl_sync(kFull, incl - cnt, k);
+        map[k * 32 + lane] = (uint16_t)(((pw >> lane) & 1u) ? base + __popc(pw & below_lane) : sigma);
+      }
     }
     if (lane == 0) a.sigma[p] = sigma;
     __syncwarp();
-    uint32_t* tab = a.peq + pr.peq_off;
-    const uint64_t words = (uint64_t)(sigma + 1) * pr.w;
-    for (uint64_t i = lane; i < words; i += 32) tab[i] = 0;
-    __syncwarp();
-    for (uint32_t q = 0; q < pr.w; ++q) {
-      const uint32_t j = q * 32 + lane;
-      const uint32_t code = j < pr.n ? map[y[j]] : 0xFFFFu;
-      const uint32_t mask = __match_any_sync(kFull, code);
-      if (code != 0xFFFFu && lane == (uint32_t)(__ffs(mask) - 1)) tab[(uint64_t)code * pr.w + q] = mask;
+    // codes of the forward job's rows x[0..mt), 16 symbols per load where the alignment of x allows, then of the
+    // reverse job's rows x[m-1] down to x[mt]; each list has kCodePadFront zero-row codes before it and
+    // kCodePadBack after it, so the main kernel reads the codes of 8 rows without a bounds check
+    {
+      const uint8_t* x = a.xs + pr.x_off;
+      uint16_t* xc = a.xcode + pr.xcf;
+      const uint32_t xh0 = (uint32_t)((16u - ((uintptr_t)x & 15u)) & 15u);
+      const uint32_t xh = xh0 < pr.mt ? xh0 : pr.mt;
+      const uint32_t xv = (pr.mt - xh) >> 4;
+      if (lane < xh) xc[lane] = map[x[lane]];
+#pragma unroll 4
+      for (uint32_t v = lane; v < xv; v += 32) {
+        const uint4 q = __ldg(reinterpret_cast<const uint4*>(x + xh + 16 * v));
+        const uint32_t in[4] = {q.x, q.y, q.z, q.w};
+        uint32_t o[8];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          o[2 * k] = (uint32_t)map[in[k] & 0xFF] | ((uint32_t)map[(in[k] >> 8) & 0xFF] << 16);
+          o[2 * k + 1] = (uint32_t)map[(in[k] >> 16) & 0xFF] | ((uint32_t)map[in[k] >> 24] << 16);
+        }
+        uint4* dst = reinterpret_cast<uint4*>(xc + xh + 16 * v);
+        dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
+        dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
+      }
+      const uint32_t i = xh + 16 * xv + lane;
+      if (lane < 16 && i < pr.mt) xc[i] = map[x[i]];
+      xc[(int)lane - (int)kCodePadFront] = (uint16_t)sigma;  // kCodePadFront == 32
+      if (lane < kCodePadBack) xc[pr.mt + lane] = (uint16_t)sigma;
+      if (pr.mt < pr.m) {
+        uint16_t* xr = a.xcode + pr.xcr;
+        const uint32_t rr = pr.m - pr.mt;
+#pragma unroll 4
+        for (uint32_t k = lane; k < rr; k += 32) xr[k] = map[x[pr.m - 1 - k]];
+        xr[(int)lane - (int)kCodePadFront] = (uint16_t)sigma;
+        if (lane < kCodePadBack) xr[rr + lane] = (uint16_t)sigma;
+      }
     }
-    const uint8_t* x = a.xs + pr.x_off;
-    uint8_t* xc = a.xcode + pr.x_off;
-    for (uint32_t i = lane; i < pr.m; i += 32) xc[i] = map[x[i]];
+    // The tables, one 32-column word q at a time: lane k holds the code of column 32q + k; ballots of the code's
+    // bits give bit planes, and the mask of symbol r is the AND over the planes of the plane (bit b of r set) or
+    // its complement (not set), restricted to the columns that exist. Lane r writes row r (rows 0..sigma, 32 rows
+    // per pass); row sigma matches no column, since the columns' codes are 0..sigma-1, and comes out zero.
+    const uint32_t nb = 32 - __clz(sigma);  // bits of the codes 0..sigma
+    switch (nb) {
+      case 1: build_tables<1>(a, pr, map, ysh, sigma, lane); break;
+      case 2: build_tables<2>(a, pr, map, ysh, sigma, lane); break;
+      case 3: build_tables<3>(a, pr, map, ysh, sigma, lane); break;
+      case 4: build_tables<4>(a, pr, map, ysh, sigma, lane); break;
+      case 5: build_tables<5>(a, pr, map, ysh, sigma, lane); break;
+      case 6: build_tables<6>(a, pr, map, ysh, sigma, lane); break;
+      case 7: build_tables<7>(a, pr, map, ysh, sigma, lane); break;
+      case 8: build_tables<8>(a, pr, map, ysh, sigma, lane); break;
+      default: build_tables<9>(a, pr, map, ysh, sigma, lane); break;
+    }
     __syncwarp();
   }
 }
 
 // ---- the persistent batch kernel --------------------------------------------------------------------------------
-__device__ __forceinline__ void add4(const uint32_t (&v)[kBK], const uint32_t (&u)[kBK], uint32_t (&s)[kBK],
-                                     uint32_t& gen) {
-  asm("add.cc.u32 %0, %5, %9;\n\t"
-      "addc.cc.u32 %1, %6, %10;\n\t"
-      "addc.cc.u32 %2, %7, %11;\n\t"
-      "addc.cc.u32 %3, %8, %12;\n\t"
-      "addc.u32 %4, 0, 0;"
-      : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(gen)
-      : "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(u[0]), "r"(u[1]), "r"(u[2]), "r"(u[3]));
-}
-__device__ __forceinline__ void inc4(uint32_t (&s)[kBK], uint32_t c) {
-  asm("add.cc.u32 %0, %0, %4;\n\t"
-      "addc.cc.u32 %1, %1, 0;\n\t"
-      "addc.cc.u32 %2, %2, 0;\n\t"
-      "addc.u32 %3, %3, 0;"
-      : "+r"(s[0]), "+r"(s[1]), "+r"(s[2]), "+r"(s[3])
-      : "r"(c));
+// S = V + U + c over the lane's 128 bits, c = cin & 1 when take is all ones and 0 when take is 0 (cin is 0 or 1);
+// cout = carry out of the lane's top bit.
+__device__ __forceinline__ void add4c(const uint32_t (&v)[kBK], const uint32_t (&u)[kBK], uint32_t cin,
+                                      uint32_t take, uint32_t (&s)[kBK], uint32_t& cout) {
+  asm("{\n\t"
+      ".reg .u32 t;\n\t"
+      "add.cc.u32 t, %5, %14;\n\t"  // carry flag = cin when take = 0xFFFFFFFF, 0 when take = 0
+      "addc.cc.u32 %0, %6, %10;\n\t"
+      "addc.cc.u32 %1, %7, %11;\n\t"
+      "addc.cc.u32 %2, %8, %12;\n\t"
+      "addc.cc.u32 %3, %9, %13;\n\t"
+      "addc.u32 %4, 0, 0;\n\t"
+      "}"
+      : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(cout)
+      : "r"(cin), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(u[0]), "r"(u[1]), "r"(u[2]), "r"(u[3]),
+        "r"(take));
 }
 
 __global__ void __launch_bounds__(kBatchWarps * 32) k_batch_main(BatchArgs a) {
@@ -135,13 +288,16 @@ __global__ void __launch_bounds__(kBatchWarps * 32) k_batch_main(BatchArgs a) {
     const uint32_t G = item.G;
     const uint32_t grp = lane / G, gl = lane % G;
     const bool has = grp < item.count;
+    BJob job{};
     BPair pr{};
     uint32_t sig = 0;
     if (has) {
-      pr = a.pairs[item.first + grp];
-      sig = a.sigma[item.first + grp];
+      job = a.jobs[item.first + grp];
+      pr = a.pairs[job.pair];
+      sig = a.sigma[job.pair];
     }
-    // lanes whose group has no pair, or whose words lie beyond the pair's row, read the all-zero row / zero words
+    const uint64_t tab = job.rev ? pr.peqr_off : pr.peq_off;
+    // lanes whose group has no job, or whose words lie beyond the pair's row, read the all-zero row / zero words
     const uint32_t w0 = gl * kBK;  // first word of this lane within its pair's row
     uint32_t sig_max = __reduce_max_sync(kFull, has ? sig : 0u);
     const bool staged = sig_max + 1 <= (uint32_t)kStageRows;
@@ -153,52 +309,55 @@ __global__ void __launch_bounds__(kBatchWarps * 32) k_batch_main(BatchArgs a) {
 #pragma unroll
         for (int k = 0; k < kBK; ++k) {
           const uint32_t q = w0 + k;
-          v[k] = (has && r <= sig && q < pr.w) ? a.peq[pr.peq_off + (uint64_t)r * pr.w + q] : 0u;
+          v[k] = (has && r <= sig && q < pr.w) ? a.peq[tab + (uint64_t)r * pr.w + q] : 0u;
         }
         *reinterpret_cast<uint4*>(&stage[r * kWarpWords + lane * kBK]) = make_uint4(v[0], v[1], v[2], v[3]);
       }
       __syncwarp();
     }
-    // top lanes of the groups: their carries must not reach the next group
-    uint32_t top = 0;
-    for (uint32_t l = G - 1; l < 32; l += G) top |= 1u << l;
-    const uint8_t* xc = a.xcode + pr.x_off;
-    const uint32_t zero_code = sig;  // the all-zero row of this pair
-    uint32_t V[kBK] = {kFull, kFull, kFull, kFull};
-    const uint32_t rows = item.rows;
-    // symbol codes are requested 8 rows before they are used (the rows beyond a pair's m read its zero row)
-    auto codes8 = [&](uint32_t i0, uint32_t (&c)[8]) {
+    auto load_p = [&](uint32_t code, uint32_t (&P)[kBK]) {
+      if (staged) {
+        const uint4 q = *reinterpret_cast<const uint4*>(&stage[code * kWarpWords + lane * kBK]);
+        P[0] = q.x; P[1] = q.y; P[2] = q.z; P[3] = q.w;
+      } else {
 #pragma unroll
-      for (int b = 0; b < 8; ++b) c[b] = (has && i0 + b < pr.m) ? (uint32_t)__ldg(xc + i0 + b) : zero_code;
+        for (int k = 0; k < kBK; ++k) {
+          const uint32_t q = w0 + k;
+          P[k] = (has && q < pr.w) ? __ldg(a.peq + tab + (uint64_t)code * pr.w + q) : 0u;
+        }
+      }
     };
-    uint32_t cq[8], nq[8];
+    // Lane gl of a group works on row t - gl at step t (a skew of one row per lane), so the carry out of its 128
+    // bits for that row reaches lane gl + 1 by one shuffle, in time for the same row at step t + 1. Rows before 0
+    // or past the job read the zero-row codes around the job's list: a row without a match leaves V unchanged.
+    // xp[r] is the code of row r - kCodePadFront; lanes without a job read the zeros at the start of xcode (code 0,
+    // whose staged row is zero for them).
+    const uint16_t* xp = has ? a.xcode + (job.rev ? pr.xcr : pr.xcf) - kCodePadFront : a.xcode;
+    const uint32_t jend = has ? job.rows + kCodePadFront : 0u;  // rows from here on read the padding only
+    auto codes8 = [&](uint32_t t0, uint32_t (&c)[8]) {
+      const uint32_t r0 = min(t0 + kCodePadFront - gl, jend);
+#pragma unroll
+      for (int b = 0; b < 8; ++b) c[b] = __ldg(xp + r0 + b);
+    };
+    uint32_t V[kBK] = {kFull, kFull, kFull, kFull};
+    uint32_t cin = 0;
+    const uint32_t take = gl ? kFull : 0u;  // the first lane of a group starts every row without a carry
+    const uint32_t steps = (item.rows + G - 1 + 7) & ~7u;
+    uint32_t cq[8], nq[8], P[kBK], Pn[kBK];
     codes8(0, cq);
-    for (uint32_t i0 = 0; i0 < rows; i0 += 8) {
-      codes8(i0 + 8, nq);
+    load_p(cq[0], Pn);
+    for (uint32_t t0 = 0; t0 < steps; t0 += 8) {
+      codes8(t0 + 8, nq);
 #pragma unroll
       for (int b = 0; b < 8; ++b) {
-        if (i0 + b >= rows) break;  // warp-uniform
-        const uint32_t code = cq[b];
-        uint32_t P[kBK];
-        if (staged) {
-          const uint4 q = *reinterpret_cast<const uint4*>(&stage[code * kWarpWords + lane * kBK]);
-          P[0] = q.x; P[1] = q.y; P[2] = q.z; P[3] = q.w;
-        } else {
 #pragma unroll
-          for (int k = 0; k < kBK; ++k) {
-            const uint32_t q = w0 + k;
-            P[k] = (has && q < pr.w) ? __ldg(a.peq + pr.peq_off + (uint64_t)code * pr.w + q) : 0u;
-          }
-        }
-        uint32_t U[kBK], S[kBK], gen;
+        for (int k = 0; k < kBK; ++k) P[k] = Pn[k];
+        load_p(b + 1 < 8 ? cq[b + 1 < 8 ? b + 1 : 0] : nq[0], Pn);  // the next step's masks, one step ahead
+        uint32_t U[kBK], S[kBK], cout;
 #pragma unroll
         for (int k = 0; k < kBK; ++k) U[k] = V[k] & P[k];
-        add4(V, U, S, gen);
-        const uint32_t prop = (S[0] & S[1] & S[2] & S[3]) == kFull;
-        const uint32_t Gb = __ballot_sync(kFull, gen), Pb = __ballot_sync(kFull, prop);
-        const uint32_t A = (Gb | Pb) & ~top, Bv = Gb & ~top;
-        const uint32_t cin = (((A + Bv) ^ A ^ Bv) >> lane) & 1u;
-        inc4(S, cin);
+        add4c(V, U, cin, take, S, cout);
+        cin = __shfl_up_sync(kFull, cout, 1);
 #pragma unroll
         for (int k = 0; k < kBK; ++k) V[k] = S[k] | (V[k] & ~P[k]);
       }
@@ -206,11 +365,66 @@ __global__ void __launch_bounds__(kBatchWarps * 32) k_batch_main(BatchArgs a) {
       for (int b = 0; b < 8; ++b) cq[b] = nq[b];
     }
     // c[m, n] = zero bits of V over the pair's n columns (bits past n stay 1), summed over the group's lanes
+    // (every lane of the warp takes part in the shuffles, whatever its group holds)
     uint32_t z = 0;
 #pragma unroll
     for (int k = 0; k < kBK; ++k) z += __popc(~V[k]);
     for (uint32_t off = 1; off < G; off <<= 1) z += __shfl_xor_sync(kFull, z, off);
-    if (has && gl == 0) a.out_lens[pr.out] = z;
+    if (has && pr.mt < pr.m) {
+      // a split pair: keep the job's final row for the combine kernel
+      uint4* dst = reinterpret_cast<uint4*>(a.fvbuf + (uint64_t)(pr.fv + job.rev) * kWarpWords + gl * kBK);
+      *dst = make_uint4(V[0], V[1], V[2], V[3]);
+    } else if (has && gl == 0) {
+      a.out_lens[pr.out] = z;
+    }
+  }
+}
+
+// Split pairs: L = n - min over j of (ones of the forward row among its first j columns + ones of the reverse row
+// among its first n - j columns). One warp per pair, prefix popcounts of the two rows in shared memory.
+__global__ void __launch_bounds__(256) k_batch_combine(BatchArgs a) {
+  __shared__ uint32_t pre_s[8][2][kWarpWords + 1];  // ones among the first 32q columns, q = 0..128
+  __shared__ uint32_t row_s[8][2][kWarpWords];
+  const uint32_t wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+  for (uint32_t k = blockIdx.x * (blockDim.x >> 5) + wid; k < a.nsplit; k += nwarps) {
+    const BPair pr = a.pairs[a.split[k]];
+    for (int d = 0; d < 2; ++d) {
+      const uint4 v4 = *reinterpret_cast<const uint4*>(a.fvbuf + (uint64_t)(pr.fv + d) * kWarpWords + lane * kBK);
+      const uint32_t v[kBK] = {v4.x, v4.y, v4.z, v4.w};
+      uint32_t c[kBK], sum = 0;
+#pragma unroll
+      for (int q = 0; q < kBK; ++q) {
+        c[q] = __popc(v[q]);
+        sum += c[q];
+        row_s[wid][d][lane * kBK + q] = v[q];
+      }
+      uint32_t incl = sum;
+      for (uint32_t off = 1; off < 32; off <<= 1) {
+        const uint32_t o = __shfl_up_sync(kFull, incl, off);
+        if (lane >= off) incl += o;
+      }
+      uint32_t run = incl - sum;
+#pragma unroll
+      for (int q = 0; q < kBK; ++q) {
+        pre_s[wid][d][lane * kBK + q] = run;
+        run += c[q];
+      }
+      if (lane == 31) pre_s[wid][d][kWarpWords] = incl;
+    }
+    __syncwarp();
+    auto ones = [&](int d, uint32_t x) {
+      const uint32_t q = x >> 5, r = x & 31;
+      return pre_s[wid][d][q] + (r ? __popc(row_s[wid][d][q] & ((1u << r) - 1u)) : 0u);
+    };
+    uint32_t best = 0xFFFFFFFFu;
+    for (uint32_t j = lane; j <= pr.n; j += 32) {
+      const uint32_t t = ones(0, j) + ones(1, pr.n - j);
+      best = t < best ? t : best;
+    }
+    best = __reduce_min_sync(kFull, best);
+    if (lane == 0) a.out_lens[pr.out] = pr.n - best;
+    __syncwarp();
   }
 }
 
@@ -222,61 +436,93 @@ inline uint32_t group_lanes(uint32_t w) {
 
 struct Plan {
   std::vector<BPair> pairs;
+  std::vector<BJob> jobs;
   std::vector<BItem> items;
+  std::vector<uint32_t> split;  // plan indices of split pairs
   uint64_t peq_words = 0;
+  uint64_t codes = kCodeZeros;  // xcode: zeros, then the jobs' padded code lists
+  uint32_t fv_slots = 0;
 };
 
+constexpr uint32_t kSplitMinRows = 256;  // pairs with fewer rows are never split
+
 // Host plan: lengths from the offsets; pairs whose words exceed one warp's 128 (n > 4096) are not handled here.
-bool make_plan(const uint64_t* x_off, const uint64_t* y_off, uint64_t count, Plan& plan, std::vector<uint64_t>& big) {
-  struct Tmp {
-    uint32_t idx, m, n, w, G;
-  };
-  std::vector<Tmp> t;
-  t.reserve(count);
+// A pair is split when its rows exceed both kSplitMinRows and the rows an average resident warp works through
+// (the batch's lane-rows spread over `warps`), i.e. when its serial chain would outlast the rest of the launch.
+bool make_plan(const uint64_t* x_off, const uint64_t* y_off, uint64_t count, uint64_t warps, Plan& plan,
+               std::vector<uint64_t>& big) {
+  uint64_t lane_rows = 0;
   for (uint64_t k = 0; k < count; ++k) {
     const uint64_t m = x_off[k + 1] - x_off[k], n = y_off[k + 1] - y_off[k];
-    if (m == 0 || n == 0) continue;  // length 0, written by the caller
+    const uint64_t w = (n + 31) / 32;
+    if (m && n && w <= (uint64_t)kWarpWords) lane_rows += m * group_lanes((uint32_t)w);
+  }
+  const uint64_t split_rows = std::max<uint64_t>(kSplitMinRows, lane_rows / (32 * std::max<uint64_t>(warps, 1)));
+  for (uint64_t k = 0; k < count; ++k) {
+    const uint64_t m = x_off[k + 1] - x_off[k], n = y_off[k + 1] - y_off[k];
+    if (m == 0 || n == 0) continue;  // length 0, written by the zeroing launch
     const uint64_t w = (n + 31) / 32;
     if (w > (uint64_t)kWarpWords || m >= (1ull << 31)) {
       big.push_back(k);
       continue;
     }
-    t.push_back({(uint32_t)k, (uint32_t)m, (uint32_t)n, (uint32_t)w, group_lanes((uint32_t)w)});
+    BPair p{};
+    p.x_off = x_off[k] - x_off[0];
+    p.y_off = y_off[k] - y_off[0];
+    p.m = (uint32_t)m;
+    p.n = (uint32_t)n;
+    p.w = (uint32_t)w;
+    p.out = (uint32_t)k;
+    const bool split = m > split_rows;
+    p.mt = split ? (uint32_t)((m + 1) / 2) : (uint32_t)m;
+    const uint64_t tab = ((std::min<uint64_t>(256u, n) + 1) * w + 3) & ~(uint64_t)3;  // whole 16-byte groups
+    p.xcf = plan.codes + kCodePadFront + ((p.x_off - plan.codes - kCodePadFront) & 15);  // = x_off modulo 16
+    plan.codes = p.xcf + p.mt + kCodePadBack;
+    if (split) {
+      p.xcr = plan.codes + kCodePadFront;
+      plan.codes = p.xcr + (p.m - p.mt) + kCodePadBack;
+    }
+    p.peq_off = plan.peq_words;
+    plan.peq_words += tab;
+    if (split) {
+      p.peqr_off = plan.peq_words;
+      plan.peq_words += tab;
+      p.fv = plan.fv_slots;
+      plan.fv_slots += 2;
+      plan.split.push_back((uint32_t)plan.pairs.size());
+    }
+    const uint32_t idx = (uint32_t)plan.pairs.size();
+    plan.pairs.push_back(p);
+    plan.jobs.push_back({idx, 0u, p.mt, 0u});
+    if (split) plan.jobs.push_back({idx, 1u, p.m - p.mt, 0u});
   }
-  // bucket by G; within a bucket, longest rows first (similar m share a warp)
-  std::sort(t.begin(), t.end(), [](const Tmp& a, const Tmp& b) {
-    if (a.G != b.G) return a.G > b.G;
-    return a.m > b.m;
+  // bucket jobs by G; within a bucket, longest first (similar rows share a warp)
+  std::vector<uint32_t> G(plan.jobs.size());
+  for (size_t j = 0; j < plan.jobs.size(); ++j) G[j] = group_lanes(plan.pairs[plan.jobs[j].pair].w);
+  std::vector<uint32_t> order(plan.jobs.size());
+  std::iota(order.begin(), order.end(), 0u);
+  std::sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) {
+    if (G[a] != G[b]) return G[a] > G[b];
+    return plan.jobs[a].rows > plan.jobs[b].rows;
   });
-  plan.pairs.resize(t.size());
-  uint64_t off = 0;
-  for (size_t i = 0; i < t.size(); ++i) {
-    BPair& p = plan.pairs[i];
-    p.x_off = x_off[t[i].idx] - x_off[0];
-    p.y_off = y_off[t[i].idx] - y_off[0];
-    p.m = t[i].m;
-    p.n = t[i].n;
-    p.w = t[i].w;
-    p.out = t[i].idx;
-    p.peq_off = off;
-    off += (uint64_t)(std::min<uint32_t>(256u, t[i].n) + 1) * t[i].w;
-  }
-  plan.peq_words = off;
-  for (size_t i = 0; i < t.size();) {
-    const uint32_t G = t[i].G, per = 32 / G;
+  std::vector<BJob> jobs(order.size());
+  for (size_t j = 0; j < order.size(); ++j) jobs[j] = plan.jobs[order[j]];
+  plan.jobs.swap(jobs);
+  for (size_t i = 0; i < plan.jobs.size();) {
+    const uint32_t g = group_lanes(plan.pairs[plan.jobs[i].pair].w), per = 32 / g;
     size_t j = i;
     uint32_t rows = 0;
-    while (j < t.size() && j - i < per && t[j].G == G) {
-      rows = std::max(rows, t[j].m);
+    while (j < plan.jobs.size() && j - i < per && group_lanes(plan.pairs[plan.jobs[j].pair].w) == g) {
+      rows = std::max(rows, plan.jobs[j].rows);
       ++j;
     }
-    plan.items.push_back({(uint32_t)i, (uint32_t)(j - i), G, rows});
+    plan.items.push_back({(uint32_t)i, (uint32_t)(j - i), g, rows});
     i = j;
   }
-  // longest items first (largest rows * words), for balance across the persistent warps
-  std::stable_sort(plan.items.begin(), plan.items.end(), [](const BItem& a, const BItem& b) {
-    return (uint64_t)a.rows * a.G > (uint64_t)b.rows * b.G;
-  });
+  // longest items first: an item holds its warp for rows + G - 1 steps whatever its G (list scheduling by the
+  // atomic ticket then approximates longest-processing-time-first over the persistent warps)
+  std::stable_sort(plan.items.begin(), plan.items.end(),
+                   [](const BItem& a, const BItem& b) { return a.rows + a.G > b.rows + b.G; });
   return true;
 }
 
@@ -300,6 +546,7 @@ static void batch_launches(lcs_ctx* c, uint64_t* d_out, uint64_t count, const Ba
   cudaMemsetAsync(d_out, 0, count * sizeof(uint64_t), st);  // empty pairs: length 0
   if (a.npairs) {
     cudaMemsetAsync(a.ticket, 0, 4, st);
+    cudaMemsetAsync(a.xcode, 0, kCodeZeros * sizeof(uint16_t), st);
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
     const unsigned prep_blocks = (unsigned)std::min<uint64_t>((a.npairs + 7) / 8, (uint64_t)sms * 8);
@@ -308,6 +555,8 @@ static void batch_launches(lcs_ctx* c, uint64_t* d_out, uint64_t count, const Ba
     const unsigned blocks = (unsigned)std::max(1, sms * std::max(per_sm, 1));
     if (marks) c->mark(1, st);
     k_batch_main<<<blocks, kBatchWarps * 32, 0, st>>>(a);
+    if (a.nsplit)
+      k_batch_combine<<<(unsigned)std::min<uint64_t>((a.nsplit + 7) / 8, (uint64_t)sms * 8), 256, 0, st>>>(a);
     if (marks) c->mark(2, st);
     c->bblocks = blocks;
   } else if (marks) {
@@ -316,9 +565,9 @@ static void batch_launches(lcs_ctx* c, uint64_t* d_out, uint64_t count, const Ba
   }
 }
 
-// Runs a batch whose xs / ys / out_lens are already on the device. The first call of a batch plans it on the host
-// and uploads the plan; a later call with the same pairs (same offsets and buffers) reuses it. Without profiling
-// the launches are captured once as a CUDA graph and replayed.
+// Runs a batch whose xs / ys / out_lens are already on the device. The first call of a batch plans it on the host,
+// uploads the plan and launches; a later call with the same pairs (same offsets and buffers) reuses the plan, and
+// without profiling its launches are captured once as a CUDA graph and replayed.
 int run_batch(lcs_ctx* c, const uint8_t* d_xs, const uint8_t* d_ys, const uint64_t* x_off, const uint64_t* y_off,
               uint64_t count, uint64_t* d_out, cudaStream_t st) {
   uint64_t key = 1469598103934665603ull;
@@ -329,46 +578,65 @@ int run_batch(lcs_ctx* c, const uint8_t* d_xs, const uint8_t* d_ys, const uint64
     key = fnv1a(key, rel, sizeof(rel));
   }
   int rc = LCS_OK;
-  if (key != c->bkey) {
+  const bool fresh = key != c->bkey;
+  if (fresh) {
     if (c->bexec) cudaGraphExecDestroy(c->bexec);
     c->bexec = nullptr;
     c->bkey = 0;
     Plan plan;
     c->bbig.clear();
-    make_plan(x_off, y_off, count, plan, c->bbig);
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_main, kBatchWarps * 32, 0);
+    make_plan(x_off, y_off, count, (uint64_t)std::max(sms, 1) * std::max(per_sm, 1) * kBatchWarps, plan, c->bbig);
     c->bcells = 0;
     for (uint64_t k = 0; k < count; ++k) c->bcells += (x_off[k + 1] - x_off[k]) * (y_off[k + 1] - y_off[k]);
-    const size_t pb = plan.pairs.size() * sizeof(BPair), ib = plan.items.size() * sizeof(BItem);
+    const size_t pb = plan.pairs.size() * sizeof(BPair), jb = plan.jobs.size() * sizeof(BJob),
+                 ib = plan.items.size() * sizeof(BItem), sb = plan.split.size() * 4;
+    const size_t jat = (pb + 255) & ~(size_t)255, iat = (jat + jb + 255) & ~(size_t)255,
+                 sat = (iat + ib + 255) & ~(size_t)255;
     if (!plan.pairs.empty()) {
-      rc = from_cuda(ensure(c->bplan, pb + ib + 256));
+      rc = from_cuda(ensure(c->bplan, sat + sb + 256));
       if (!rc) rc = from_cuda(ensure(c->bsig, plan.pairs.size() * 4 + 4));
-      if (!rc) rc = from_cuda(ensure(c->bxcode, std::max<uint64_t>(x_off[count] - x_off[0], 1)));
+      if (!rc) rc = from_cuda(ensure(c->bxcode, (plan.codes + 16) * 2));
       if (!rc) rc = from_cuda(ensure(c->bpeq, plan.peq_words * 4 + 4));
+      if (!rc) rc = from_cuda(ensure(c->bfv, ((uint64_t)plan.fv_slots * kWarpWords + 4) * 4));
       if (rc) return rc;
       // (copies from pageable memory: the runtime has staged the data when the call returns)
-      rc = from_cuda(cudaMemcpyAsync(c->bplan.p, plan.pairs.data(), pb, cudaMemcpyHostToDevice, st));
-      if (!rc) rc = from_cuda(cudaMemcpyAsync((char*)c->bplan.p + pb, plan.items.data(), ib, cudaMemcpyHostToDevice, st));
+      char* base = (char*)c->bplan.p;
+      rc = from_cuda(cudaMemcpyAsync(base, plan.pairs.data(), pb, cudaMemcpyHostToDevice, st));
+      if (!rc) rc = from_cuda(cudaMemcpyAsync(base + jat, plan.jobs.data(), jb, cudaMemcpyHostToDevice, st));
+      if (!rc) rc = from_cuda(cudaMemcpyAsync(base + iat, plan.items.data(), ib, cudaMemcpyHostToDevice, st));
+      if (!rc && sb) rc = from_cuda(cudaMemcpyAsync(base + sat, plan.split.data(), sb, cudaMemcpyHostToDevice, st));
       if (rc) return rc;
     }
     c->bnpairs = plan.pairs.size();
     c->bnitems = plan.items.size();
-    c->bpairs_bytes = pb;
+    c->bnsplit = plan.split.size();
+    c->bjobs_at = jat;
+    c->bitems_at = iat;
+    c->bsplit_at = sat;
     c->bkey = key;
   }
   BatchArgs a{};
   a.xs = d_xs;
   a.ys = d_ys;
   a.pairs = (const BPair*)c->bplan.p;
-  a.items = (const BItem*)((char*)c->bplan.p + c->bpairs_bytes);
+  a.jobs = (const BJob*)((char*)c->bplan.p + c->bjobs_at);
+  a.items = (const BItem*)((char*)c->bplan.p + c->bitems_at);
+  a.split = (const uint32_t*)((char*)c->bplan.p + c->bsplit_at);
+  a.fvbuf = (uint32_t*)c->bfv.p;
   a.sigma = (uint32_t*)c->bsig.p;
-  a.xcode = (uint8_t*)c->bxcode.p;
+  // xcode + xcf is then a multiple of 32 bytes where xs + x_off is a multiple of 16
+  a.xcode = (uint16_t*)c->bxcode.p + ((uintptr_t)d_xs & 15u);
   a.peq = (uint32_t*)c->bpeq.p;
   a.out_lens = d_out;
   a.ticket = (uint32_t*)((char*)c->small.p + kOffTicket);
   a.npairs = (uint32_t)c->bnpairs;
   a.nitems = (uint32_t)c->bnitems;
-  if (c->prof) {
-    batch_launches(c, d_out, count, a, st, true);
+  a.nsplit = (uint32_t)c->bnsplit;
+  if (c->prof || fresh) {
+    batch_launches(c, d_out, count, a, st, c->prof);
     rc = from_cuda(cudaGetLastError());
   } else {
     if (!c->bexec) {

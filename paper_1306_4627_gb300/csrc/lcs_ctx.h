@@ -43,12 +43,13 @@ struct lcs_ctx {
   lcs::DBuf small, x, y, out;
   lcs::DBuf xoff_f, xoff_r, xcode, peq_f, peq_r, carry_f, carry_r, fv_f, fv_r, T, snap_f, snap_r;
   lcs::DBuf colsum, ent, ext, nch, entcnt, sel, chars;
-  lcs::DBuf bplan, bsig, bxcode, bpeq, bout;  // batch: plan, per-pair alphabet sizes, codes, masks, lengths
+  lcs::DBuf bplan, bsig, bxcode, bpeq, bout, bfv;  // batch: plan, alphabet sizes, codes, masks, lengths, half rows
   // batch: the last plan's launches captured as a CUDA graph, replayed while the same batch is submitted again
   uint64_t bkey = 0;
   cudaGraphExec_t bexec = nullptr;
   std::vector<uint64_t> bbig;
-  uint64_t bcells = 0, bblocks = 0, bnpairs = 0, bnitems = 0, bpairs_bytes = 0;
+  uint64_t bcells = 0, bblocks = 0, bnpairs = 0, bnitems = 0, bnsplit = 0;
+  uint64_t bjobs_at = 0, bitems_at = 0, bsplit_at = 0;  // byte offsets of the plan's parts in bplan
   cudaStream_t cap_stream = nullptr;
   uint64_t host_word[1] = {0};
   // stage events of the last profiled call: [0] start, [1] fill start, [2] fill end, [3] end
@@ -73,7 +74,7 @@ struct lcs_ctx {
     cap_stream = nullptr;
     lcs::DBuf* all[] = {&small, &x, &y, &out, &xoff_f, &xoff_r, &xcode, &peq_f, &peq_r, &carry_f, &carry_r,
                         &fv_f, &fv_r, &T, &snap_f, &snap_r, &colsum, &ent, &ext, &nch, &entcnt, &sel, &chars,
-                        &bplan, &bsig, &bxcode, &bpeq, &bout};
+                        &bplan, &bsig, &bxcode, &bpeq, &bout, &bfv};
     for (lcs::DBuf* b : all) lcs::release(*b);
   }
 };

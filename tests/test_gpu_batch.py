@@ -80,3 +80,21 @@ def test_batch_10000_pairs_vs_oracle(ctx, oracle):
     got = ctx.batch(pairs)
     want = np.array([oracle.lcs_length(x, y) for x, y in pairs])
     assert np.array_equal(got.astype(np.int64), want)
+
+
+@pytest.mark.parametrize("sigma", [4, 20, 256])
+def test_batch_split_pairs(ctx, oracle, sigma):
+    """Pairs with many rows run as a forward top half and a reversed bottom half, joined at the middle row
+    (c[mt, j] + LCS of the bottom rows with Y[j+1..n], maximised over j): odd and even m, ragged n, unrelated and
+    closely related strings."""
+    shapes = [(256, 300), (257, 257), (258, 31), (301, 4096), (511, 1000), (1024, 33), (2047, 2049), (4096, 4096),
+              (3000, 129)]
+    pairs = []
+    for k, (m, n) in enumerate(shapes):
+        pairs.append(gen.pair_uniform(m, n, sigma, seed=4400 + 10 * sigma + k))
+        x, _ = gen.pair_uniform(m, 1, sigma, seed=4500 + 10 * sigma + k)
+        pairs.append((x, gen.mutate(x, seed=4600 + 10 * sigma + k, alphabet=gen.ALPHABETS[sigma], out_len=min(m, 4096))))
+    want = [oracle.lcs_length(x, y) for x, y in pairs]
+    for _ in range(3):  # first call plans and launches; the repeats replay the recorded launches
+        got = ctx.batch(pairs)
+        assert [int(v) for v in got] == want
