@@ -45,7 +45,9 @@ struct lcs_ctx {
   lcs::DBuf colsum, ent, ext, nch, entcnt, sel, chars;
   lcs::DBuf bplan, bsig, bxcode, bpeq, bout, bfv;  // batch: plan, alphabet sizes, codes, masks, lengths, half rows
   // batch: the last plan's launches captured as a CUDA graph, replayed while the same batch is submitted again
-  uint64_t bkey = 0;
+  bool bvalid = false;
+  uint64_t bptrs[4] = {0, 0, 0, 0};
+  std::vector<uint64_t> boffs;  // relative offsets of the planned batch, x and y interleaved
   cudaGraphExec_t bexec = nullptr;
   std::vector<uint64_t> bbig;
   uint64_t bcells = 0, bblocks = 0, bnpairs = 0, bnitems = 0, bnsplit = 0;
@@ -70,6 +72,7 @@ struct lcs_ctx {
   void release_all() {
     if (bexec) cudaGraphExecDestroy(bexec);
     bexec = nullptr;
+    bvalid = false;
     if (cap_stream) cudaStreamDestroy(cap_stream);
     cap_stream = nullptr;
     lcs::DBuf* all[] = {&small, &x, &y, &out, &xoff_f, &xoff_r, &xcode, &peq_f, &peq_r, &carry_f, &carry_r,
