@@ -496,6 +496,73 @@ def run_serve_workload(args):
     ctx.close()
 
 
+# The paper's experiment (Table 1): parent length M (rows, X) x child length N (columns, Y), DNA strings.
+TABLE1_SHAPES = [(10, 5), (100, 10), (200, 30), (500, 80), (800, 100), (1000, 150), (2000, 200), (5000, 200),
+                 (5000, 400), (5000, 800), (5000, 1000), (10000, 1000), (10000, 1500)]
+
+
+def _time_reps(fn, min_s: float = 0.05, max_reps: int = 200) -> float:
+    """Median seconds of fn() over repetitions that add up to at least min_s (one warm call first)."""
+    fn()
+    ts = []
+    while len(ts) < max_reps and (sum(ts) < min_s or len(ts) < 3):
+        t0 = time.perf_counter()
+        fn()
+        ts.append(time.perf_counter() - t0)
+    return float(np.median(ts))
+
+
+def run_table1_workload(args):
+    """The shapes of the paper's Table 1 with uniform DNA strings: per shape the traceback through the host-buffer
+    call (length and LCS string, copies included), its device time, the serial oracle on one core and the
+    multi-threaded oracle (the paper's column-block parallel fill) on all host cores. The paper's speedup column
+    is parallel CPU time against serial CPU time; the GPU columns are this library."""
+    from oracle import oracle
+    from paper_1306_4627_gb300 import gen, lcs
+    oracle.build()
+    cores = os.cpu_count() or 1
+    ctx = lcs.Context(0)
+    rows, tot_cells, tot_gpu, tot_par = [], 0, 0.0, 0.0
+    for k, (m, n) in enumerate(TABLE1_SHAPES):
+        x, y = gen.pair_uniform(m, n, 4, seed=gen.BASE_SEED + 100 + k)
+        s_gpu = ctx.traceback(x, y)
+        parity = s_gpu == oracle.lcs_traceback(x, y) == oracle.lcs_traceback_par(x, y, cores)
+        t_gpu = _time_reps(lambda: ctx.traceback(x, y))
+        ctx.set_profiling(True)
+        dev, stages = [], []
+        for _ in range(max(3, args.steps)):
+            ctx.traceback(x, y)
+            p = ctx.last_profile()
+            dev.append(p["total_ms"])
+            stages.append((p["prep_ms"], p["fill_ms"], p["trace_ms"]))
+        ctx.set_profiling(False)
+        st = np.median(np.array(stages), axis=0)
+        t_cpu1 = _time_reps(lambda: oracle.lcs_traceback(x, y), min_s=0.02)
+        t_cpun = _time_reps(lambda: oracle.lcs_traceback_par(x, y, cores), min_s=0.02)
+        rows.append({"M": m, "N": n, "lcs_length": len(s_gpu), "parity_with_oracle": bool(parity),
+                     "gpu_e2e_ms": t_gpu * 1e3, "gpu_device_ms": float(np.median(dev)),
+                     "gpu_stages_ms": {"prep": float(st[0]), "fill": float(st[1]), "trace": float(st[2])},
+                     "cpu_1core_ms": t_cpu1 * 1e3, f"cpu_{cores}core_ms": t_cpun * 1e3,
+                     "cpu_parallel_speedup": t_cpu1 / t_cpun, "gpu_e2e_vs_cpu_1core": t_cpu1 / t_gpu})
+        tot_cells += m * n
+        tot_gpu += t_gpu
+        tot_par += t_cpun
+        print(json.dumps({"table1_shape": rows[-1]}), file=sys.stderr, flush=True)
+    line = {
+        "metric": METRIC, "value": tot_cells / tot_gpu / 1e9, "unit": "GCUPS", "n_gpus": 1, "steps": args.steps,
+        "warmup": 1, "ms_per_step": tot_gpu * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "the 13 shapes of the paper's Table 1 (M x N from 10x5 to 10000x1500), uniform DNA, "
+                               "traceback through the host-buffer call; value = all cells / summed per-call time"},
+        "sweep": rows,
+        "cpu_baseline": {"value": tot_cells / tot_par / 1e9, "unit": "GCUPS", "cores": cores, "kind": "oracle",
+                         "sample": "all 13 shapes, multi-threaded oracle (column blocks over host threads)"},
+        "all_parity": all(r["parity_with_oracle"] for r in rows),
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     global M, N
     ap = argparse.ArgumentParser()
@@ -509,8 +576,9 @@ def main():
     ap.add_argument("--m", type=int, default=M, help="rows (profiling of smaller cases only)")
     ap.add_argument("--n", type=int, default=N, help="columns (profiling of smaller cases only)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="pair", choices=["pair", "batch", "long", "serve"],
-                    help="pair: the 65536^2 traceback step (default); batch: 10000 pairs; long: 262144^2 length")
+    ap.add_argument("--workload", default="pair", choices=["pair", "batch", "long", "serve", "table1"],
+                    help="pair: the 65536^2 traceback step (default); batch: 10000 pairs; long: 262144^2 length; "
+                         "serve: Poisson request streams; table1: the shapes of the paper's Table 1")
     ap.add_argument("--seq-sample", type=int, default=400, help="pairs timed as sequential single-pair launches")
     ap.add_argument("--rates", default="1000,3000,10000,30000,100000", help="serving: request rates per second")
     ap.add_argument("--serve-count", type=int, default=3000, help="serving: requests per rate")
@@ -526,6 +594,8 @@ def main():
         run_long_workload(args)
     elif args.workload == "serve":
         run_serve_workload(args)
+    elif args.workload == "table1":
+        run_table1_workload(args)
     else:
         run_gpu(args)
 

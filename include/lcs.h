@@ -129,6 +129,21 @@ LCS_API int lcs_traceback(lcs_ctx* ctx, const uint8_t* x, uint64_t m, const uint
 LCS_API int lcs_traceback_dev(lcs_ctx* ctx, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, uint64_t n,
                       uint8_t* d_out, uint64_t out_cap, uint64_t* d_out_len, void* stream);
 
+/* ---- full tables (paper §I.C: LCS-length returns the tables c and b) ------------------------------------------ */
+
+/* c[i][j] = length of an LCS of X[1..i] and Y[1..j] for 0 <= i <= m, 0 <= j <= n, written row-major to
+ * c[i * (n + 1) + j] ((m + 1) * (n + 1) uint32 values). b[i-1][j-1] for 1 <= i <= m, 1 <= j <= n is the paper's
+ * arrow, written row-major to b[(i - 1) * n + (j - 1)] (m * n bytes): 1 = diagonal (x_i = y_j), 2 = up
+ * (c[i-1][j] >= c[i][j-1]), 3 = left. b may be NULL when m * n = 0. Meant for inspection of small and medium
+ * problems: the device holds both tables plus an m*n/8-byte direction bitmap (LCS_ERR_NOMEM when that does not
+ * fit). Host buffers, blocking. */
+LCS_API int lcs_tables(lcs_ctx* ctx, const uint8_t* x, uint64_t m, const uint8_t* y, uint64_t n, uint32_t* c,
+                       uint8_t* b);
+
+/* The same into device buffers d_c and d_b, asynchronous in `stream` (NULL: the context's stream). */
+LCS_API int lcs_tables_dev(lcs_ctx* ctx, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, uint64_t n,
+                           uint32_t* d_c, uint8_t* d_b, void* stream);
+
 /* ---- batch: many independent pairs, lengths only (c[m_k, n_k] for every pair k) ------------------------------- */
 
 /* Pair k is x = xs[x_off[k] .. x_off[k+1]) and y = ys[y_off[k] .. y_off[k+1]) (count+1 offsets each, non-

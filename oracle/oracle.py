@@ -5,6 +5,8 @@ no code with the CUDA library and never calls it.
 
 * `lcs_length`, `lcs_traceback`, `lcs_tables`: ctypes calls into `lcs_oracle.c`, the literal LCS-length (§I.C)
   and Print-LCS (§I.D) of Dash & Nayak with the paper's tie-break (UP when c[i-1,j] >= c[i,j-1]).
+* `lcs_traceback_par`: `lcs_oracle_par.c`, the same fill split into column blocks over host threads (the
+  paper's parallel algorithm, §II.A-B); a CPU baseline for the paper's own experiment (Table 1).
 * `brute_force`: the exhaustive method the paper contrasts with dynamic programming (§I and §I.A): enumerate all
   2^m subsequences of X, keep those that are also subsequences of Y, and return the largest length together with
   the set of all common subsequences of that length. Exponential; only for m <= 16.
@@ -21,6 +23,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lcs_oracle.c")
+_SRC_PAR = os.path.join(_HERE, "lcs_oracle_par.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liblcs_oracle.so")
 _lock = threading.Lock()
@@ -30,11 +33,14 @@ DIAG, UP, LEFT = 1, 2, 3
 
 
 def build(force: bool = False) -> str:
-    """Compile lcs_oracle.c with gcc into oracle/_build/liblcs_oracle.so (plain -O2, no tuning)."""
+    """Compile lcs_oracle.c and lcs_oracle_par.c with gcc into oracle/_build/liblcs_oracle.so (plain -O2, no
+    tuning)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_PAR))
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-pthread", "-shared", "-fPIC", "-o", tmp, _SRC,
+                               _SRC_PAR])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -51,6 +57,8 @@ def _load():
             lib.oracle_lcs_traceback.restype = ctypes.c_int
             lib.oracle_lcs_tables.argtypes = [u8p, u64, u8p, u64, ctypes.POINTER(ctypes.c_uint32), u8p]
             lib.oracle_lcs_tables.restype = ctypes.c_int
+            lib.oracle_lcs_traceback_par.argtypes = [u8p, u64, u8p, u64, u8p, u64, ctypes.POINTER(u64), ctypes.c_int]
+            lib.oracle_lcs_traceback_par.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -96,6 +104,22 @@ def lcs_tables(x, y) -> tuple[np.ndarray, np.ndarray]:
     b = np.zeros(max(1, m * n), dtype=np.uint8)
     _load().oracle_lcs_tables(_ptr(x), m, _ptr(y), n, c.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), _ptr(b))
     return c.reshape(m + 1, n + 1), b[: m * n].reshape(m, n)
+
+
+def lcs_traceback_par(x, y, threads: int) -> bytes:
+    """The same LCS as lcs_traceback, with the table filled by `threads` host threads in column blocks (the
+    paper's parallel algorithm, §II.A-B). Returns the string; its length is c[m, n]."""
+    x, y = _u8(x), _u8(y)
+    cap = max(1, min(len(x), len(y)))
+    out = np.zeros(cap, dtype=np.uint8)
+    n_out = ctypes.c_uint64(0)
+    rc = _load().oracle_lcs_traceback_par(_ptr(x), len(x), _ptr(y), len(y), _ptr(out), cap, ctypes.byref(n_out),
+                                          int(threads))
+    if rc == -1:
+        raise MemoryError("oracle: out of memory")
+    if rc != 0:
+        raise RuntimeError(f"oracle_lcs_traceback_par failed: {rc}")
+    return out[: n_out.value].tobytes()
 
 
 def is_subsequence(z: bytes, s: bytes) -> bool:

@@ -299,6 +299,52 @@ int run_traceback(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y
   return rc;
 }
 
+// The full tables of LCS-length (§I.C): the forward fill over all m rows in traceback mode gives the direction
+// bitmap; c and b are expanded from it (launch_tables). d_c: (m+1)(n+1) words, d_b: m*n bytes, row-major.
+int run_tables(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, uint64_t n, uint32_t* d_c,
+               uint8_t* d_b, cudaStream_t st) {
+  if (m == 0 || n == 0) return from_cuda(cudaMemsetAsync(d_c, 0, (m + 1) * (n + 1) * sizeof(uint32_t), st));
+  const uint32_t B = c->fill_B_tb;
+  const Geo g = geo_for(n);
+  const uint64_t Rf = (m + B - 1) / B;
+  const uint64_t nwarps = g.nblocks * kFillWarps;
+  const size_t t_bytes = (size_t)nwarps * (Rf + 31) * 32 * B * 4;
+  int rc = prep_y(c, d_y, n, g, false, st);
+  if (!rc) rc = from_cuda(ensure(c->T, t_bytes));
+  if (!rc) rc = from_cuda(ensure(c->xoff_f, (Rf + kPadRowblocks + kPadBackRowblocks) * B * 4));
+  if (!rc) rc = from_cuda(ensure(c->carry_f, g.nblocks * Rf * 4));
+  if (!rc) rc = from_cuda(ensure(c->snap_f, g.wpad * 4));
+  if (!rc) rc = from_cuda(ensure(c->colsum, tables_sum_words(m, n) * 4));
+  if (rc) return rc;
+  rc = from_cuda(launch_xoff(d_x, m, false, 0, Rf, B, c->codemap(), c->sigma(), (uint32_t*)c->xoff_f.p, nullptr,
+                             st));
+  if (!rc) rc = from_cuda(cudaMemsetAsync(c->carry_f.p, 0, g.nblocks * Rf * 4, st));
+  if (!rc) rc = from_cuda(cudaMemsetAsync(c->len_acc(), 0, sizeof(unsigned long long), st));
+  if (rc) return rc;
+  FillJob job{};
+  job.xoff = (const uint32_t*)c->xoff_f.p;
+  job.peq = (const uint32_t*)c->peq_f.p;
+  job.sigma_rows = c->sigma();
+  job.carry = (uint32_t*)c->carry_f.p;
+  job.T = (uint32_t*)c->T.p;
+  job.snap = (uint32_t*)c->snap_f.p;  // a snapshot period past the last row: nothing is stored
+  job.snap_rb = (uint32_t)(Rf + 1);
+  job.len_acc = c->len_acc();
+  job.R = Rf;
+  job.wpad = g.wpad;
+  job.nblocks_total = (uint32_t)g.nblocks;
+  rc = run_fill(c, &job, 1, true, B, st);
+  if (rc) return rc;
+  TraceArgs t{};
+  t.T = (const uint32_t*)c->T.p;
+  t.x = d_x;
+  t.m = m;
+  t.n = n;
+  t.R = Rf;
+  t.B = B;
+  return from_cuda(launch_tables(t, d_y, (uint32_t*)c->colsum.p, d_c, d_b, st));
+}
+
 }  // namespace lcs
 
 // ---- C ABI -----------------------------------------------------------------------------------------------------
@@ -460,5 +506,49 @@ extern "C" int lcs_traceback(lcs_ctx* c, const uint8_t* x, uint64_t m, const uin
   *out_len = L;
   if (L > out_cap) return LCS_ERR_CAPACITY;
   if (L) rc = from_cuda(cudaMemcpy(out, c->out.p, L, cudaMemcpyDeviceToHost));
+  return rc;
+}
+
+// Table sizes in bytes; false when they do not fit in 64 bits.
+static bool table_bytes(uint64_t m, uint64_t n, uint64_t* cb, uint64_t* bb) {
+  if (m >= (1ull << 32) || n >= (1ull << 32) || m > 65535ull * 64) return false;  // row chunks: one grid row each
+  const unsigned __int128 cells = (unsigned __int128)(m + 1) * (n + 1);
+  if (cells * 4 >= ((unsigned __int128)1 << 63)) return false;
+  *cb = (uint64_t)cells * 4;
+  *bb = m * n;
+  return true;
+}
+
+extern "C" int lcs_tables_dev(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, uint64_t n,
+                              uint32_t* d_c, uint8_t* d_b, void* stream) {
+  uint64_t cb = 0, bb = 0;
+  if (!c || !d_c || (m && !d_x) || (n && !d_y) || !table_bytes(m, n, &cb, &bb) || (bb && !d_b))
+    return LCS_ERR_INVALID;
+  std::lock_guard<std::mutex> g(c->mu);
+  cudaSetDevice(c->device);
+  return run_tables(c, d_x, m, d_y, n, d_c, d_b, pick(c, stream));
+}
+
+extern "C" int lcs_tables(lcs_ctx* c, const uint8_t* x, uint64_t m, const uint8_t* y, uint64_t n, uint32_t* cout,
+                          uint8_t* bout) {
+  uint64_t cb = 0, bb = 0;
+  if (!c || !cout || (m && !x) || (n && !y) || !table_bytes(m, n, &cb, &bb) || (bb && !bout))
+    return LCS_ERR_INVALID;
+  std::lock_guard<std::mutex> g(c->mu);
+  cudaSetDevice(c->device);
+  void* dc = nullptr;
+  void* db = nullptr;
+  int rc = stage_inputs(c, x, m, y, n);
+  if (!rc) rc = from_cuda(cudaMalloc(&dc, cb));
+  if (!rc && bb) rc = from_cuda(cudaMalloc(&db, bb));
+  if (!rc)
+    rc = run_tables(c, (const uint8_t*)c->x.p, m, (const uint8_t*)c->y.p, n, (uint32_t*)dc, (uint8_t*)db,
+                    c->stream);
+  if (!rc) rc = from_cuda(cudaStreamSynchronize(c->stream));
+  if (!rc) rc = take_status(c);
+  if (!rc) rc = from_cuda(cudaMemcpy(cout, dc, cb, cudaMemcpyDeviceToHost));
+  if (!rc && bb) rc = from_cuda(cudaMemcpy(bout, db, bb, cudaMemcpyDeviceToHost));
+  if (dc) cudaFree(dc);
+  if (db) cudaFree(db);
   return rc;
 }

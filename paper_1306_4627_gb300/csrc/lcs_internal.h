@@ -104,6 +104,10 @@ cudaError_t launch_combine(const uint32_t* vf, const uint32_t* vr, uint64_t n, u
                            uint32_t* colsum, unsigned long long* out_len, cudaStream_t st);
 // traceback
 cudaError_t launch_traceback(const TraceArgs& t, cudaStream_t st);
+// full tables c, b from the forward bitmap (t.T, t.x, t.m, t.n, t.R, t.B); sums holds tables_sum_words words
+cudaError_t launch_tables(const TraceArgs& t, const uint8_t* y, uint32_t* sums, uint32_t* c, uint8_t* b,
+                          cudaStream_t st);
+uint64_t tables_sum_words(uint64_t m, uint64_t n);
 // batch
 struct BatchPlan;
 // misc

@@ -112,9 +112,10 @@ __global__ void k_corr_cols(TraceArgs a) {
 // Bitmap layout of the fill kernel: warp g's chunk for step t holds, for each of its 32 lanes, the B words of the
 // row-block that lane processed at that step (lane l at step t: row-block t - l), as [B/4][32 lanes][4 words].
 __device__ __forceinline__ uint32_t t_word(const TraceArgs& a, uint64_t i, uint64_t Q) {
-  const uint64_t r = (i - 1) / a.B, b = (i - 1) % a.B;
-  const uint64_t chunk = (Q >> 5) * (a.R + 31) + r + (Q & 31);
-  return a.T[chunk * 32 * a.B + (b >> 2) * 128 + (Q & 31) * 4 + (b & 3)];
+  const uint32_t lb = 31u - __clz(a.B);  // B is a power of two (8 or 16)
+  const uint32_t i0 = (uint32_t)(i - 1), b = i0 & (a.B - 1);
+  const uint64_t chunk = (Q >> 5) * (a.R + 31) + (i0 >> lb) + (Q & 31);
+  return a.T[(chunk << (5 + lb)) + (b >> 2) * 128 + (Q & 31) * 4 + (b & 3)];
 }
 
 __device__ __forceinline__ uint32_t p_word(const TraceArgs& a, uint32_t code, int64_t q) {
@@ -122,37 +123,65 @@ __device__ __forceinline__ uint32_t p_word(const TraceArgs& a, uint32_t code, in
 }
 
 // Walks rows hi..lo+1 from column e; returns the exit column (at row lo); writes emitted symbols to out_chars.
+// The rows are taken 8 at a time: the symbol codes, bitmap words and match-mask words of the next 8 rows at the
+// walk's current 32-column word are requested together (the walk usually stays in one word for many rows), so
+// the loads of a group overlap; a row whose scan leaves that word reads its words directly.
 __device__ uint64_t walk_segment(const TraceArgs& a, uint64_t hi, uint64_t lo, uint64_t e, uint8_t* out_chars,
                                  uint32_t* out_cnt) {
+  constexpr int kG = 8;
   uint64_t i = hi, j = e;
   uint32_t cnt = 0;
   while (i > lo && j > 0) {
-    const uint32_t code = a.xcode[i - 1];
-    int64_t Q = (int64_t)(j >> 5);
-    uint32_t mask = kFull >> (31 - (uint32_t)(j & 31));
-    uint32_t pm = 0, stop = 0;
-    for (;;) {
-      const uint32_t dv = t_word(a, i, (uint64_t)Q);
-      pm = (p_word(a, code, Q) << 1) | (p_word(a, code, Q - 1) >> 31);
-      stop = (pm | ~dv) & mask;
-      if (Q == 0) stop &= ~1u;  // column 0 is the border
-      if (stop || Q == 0) break;
-      --Q;
-      mask = kFull;
+    const int64_t Qg = (int64_t)(j >> 5);
+    uint32_t cd[kG], dv[kG], pa[kG], pb[kG];
+#pragma unroll
+    for (int k = 0; k < kG; ++k) {
+      const bool ok = i > lo + (uint64_t)k;
+      cd[k] = ok ? a.xcode[i - k - 1] : 0u;
+      dv[k] = ok ? t_word(a, i - k, (uint64_t)Qg) : 0u;
     }
-    if (!stop) {
-      j = 0;
-      break;
+#pragma unroll
+    for (int k = 0; k < kG; ++k) {
+      const bool ok = i > lo + (uint64_t)k;
+      pa[k] = ok ? p_word(a, cd[k], Qg) : 0u;
+      pb[k] = ok ? p_word(a, cd[k], Qg - 1) : 0u;
     }
-    const uint32_t bit = 31u - __clz(stop);
-    const uint64_t c = ((uint64_t)Q << 5) + bit;
-    if ((pm >> bit) & 1u) {
-      out_chars[cnt++] = a.x[i - 1];
-      j = c - 1;
-    } else {
-      j = c;
+#pragma unroll
+    for (int k = 0; k < kG; ++k) {
+      if (i <= lo || j == 0) break;
+      const uint32_t code = cd[k];
+      int64_t Q = (int64_t)(j >> 5);
+      uint32_t mask = kFull >> (31 - (uint32_t)(j & 31));
+      uint32_t pm = 0, stop = 0;
+      for (;;) {
+        uint32_t d;
+        if (Q == Qg) {
+          d = dv[k];
+          pm = (pa[k] << 1) | (pb[k] >> 31);
+        } else {
+          d = t_word(a, i, (uint64_t)Q);
+          pm = (p_word(a, code, Q) << 1) | (p_word(a, code, Q - 1) >> 31);
+        }
+        stop = (pm | ~d) & mask;
+        if (Q == 0) stop &= ~1u;  // column 0 is the border
+        if (stop || Q == 0) break;
+        --Q;
+        mask = kFull;
+      }
+      if (!stop) {
+        j = 0;
+        break;
+      }
+      const uint32_t bit = 31u - __clz(stop);
+      const uint64_t c = ((uint64_t)Q << 5) + bit;
+      if ((pm >> bit) & 1u) {
+        out_chars[cnt++] = a.x[i - 1];
+        j = c - 1;
+      } else {
+        j = c;
+      }
+      --i;
     }
-    --i;
   }
   *out_cnt = cnt;
   return j;
@@ -260,6 +289,55 @@ __global__ void k_seed_last(TraceArgs a) {
   a.ent_cnt[a.S - 1] = 1;
 }
 
+// ---- the full tables c and b of LCS-length (§I.C) from the forward bitmap ----------------------------------------
+// c[i,j] = c[i-1,j] + dv(i,j), where dv(i,j) = c[i,j] - c[i-1,j] is bit j % 32 of T-frame word j / 32 of row i
+// (column 0 reads 0). Rows are cut into chunks of kTabChunk rows: the chunk sums of dv per column, their exclusive
+// prefix over the chunks (the value of c at each chunk's top row), then every chunk expanded row by row. b[i,j] is
+// DIAG when x_i = y_j, else UP when dv(i,j) = 0 (c[i-1,j] >= c[i,j-1]) and LEFT when it is 1.
+constexpr uint32_t kTabChunk = 64;
+
+__device__ __forceinline__ uint32_t dv_bit(const TraceArgs& a, uint64_t i, uint64_t j) {
+  return (t_word(a, i, j >> 5) >> (j & 31)) & 1u;
+}
+
+__global__ void k_tab_sum(TraceArgs a, uint32_t* sums) {
+  const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t k = blockIdx.y;
+  if (j > a.n) return;
+  const uint64_t i0 = k * kTabChunk + 1, i1 = i0 + kTabChunk <= a.m + 1 ? i0 + kTabChunk : a.m + 1;
+  uint32_t s = 0;
+  for (uint64_t i = i0; i < i1; ++i) s += dv_bit(a, i, j);
+  sums[k * (a.n + 1) + j] = s;
+}
+
+__global__ void k_tab_scan(uint64_t n, uint64_t chunks, uint32_t* sums) {
+  const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j > n) return;
+  uint32_t run = 0;
+  for (uint64_t k = 0; k < chunks; ++k) {
+    const uint32_t t = sums[k * (n + 1) + j];
+    sums[k * (n + 1) + j] = run;
+    run += t;
+  }
+}
+
+__global__ void k_tab_expand(TraceArgs a, const uint8_t* y, const uint32_t* sums, uint32_t* c, uint8_t* b) {
+  const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t k = blockIdx.y;
+  if (j > a.n) return;
+  const uint64_t w = a.n + 1;
+  if (k == 0) c[j] = 0;  // row 0
+  const uint64_t i0 = k * kTabChunk + 1, i1 = i0 + kTabChunk <= a.m + 1 ? i0 + kTabChunk : a.m + 1;
+  const uint32_t yj = j > 0 ? y[j - 1] : 0u;
+  uint32_t cc = sums[k * w + j];
+  for (uint64_t i = i0; i < i1; ++i) {
+    const uint32_t d = dv_bit(a, i, j);
+    cc += d;
+    c[i * w + j] = cc;
+    if (j > 0) b[(i - 1) * a.n + (j - 1)] = a.x[i - 1] == yj ? 1u : (d ? 3u : 2u);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_combine(const uint32_t* vf, const uint32_t* vr, uint64_t n, uint64_t w, uint32_t* colsum,
@@ -290,5 +368,17 @@ cudaError_t launch_traceback(const TraceArgs& a, cudaStream_t st) {
   k_finalize<<<(unsigned)a.S, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
+
+cudaError_t launch_tables(const TraceArgs& a, const uint8_t* y, uint32_t* sums, uint32_t* c, uint8_t* b,
+                          cudaStream_t st) {
+  const uint64_t chunks = (a.m + kTabChunk - 1) / kTabChunk;
+  const unsigned gx = (unsigned)((a.n + 1 + 255) / 256);
+  k_tab_sum<<<dim3(gx, (unsigned)chunks), 256, 0, st>>>(a, sums);
+  k_tab_scan<<<gx, 256, 0, st>>>(a.n, chunks, sums);
+  k_tab_expand<<<dim3(gx, (unsigned)chunks), 256, 0, st>>>(a, y, sums, c, b);
+  return cudaGetLastError();
+}
+
+uint64_t tables_sum_words(uint64_t m, uint64_t n) { return ((m + kTabChunk - 1) / kTabChunk) * (n + 1); }
 
 }  // namespace lcs

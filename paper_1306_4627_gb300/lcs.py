@@ -24,7 +24,7 @@ EXPORTS = (
     "lcs_strerror", "lcs_ctx_create", "lcs_ctx_destroy", "lcs_ctx_sync", "lcs_length", "lcs_length_dev",
     "lcs_traceback", "lcs_traceback_dev", "lcs_batch", "lcs_batch_dev", "lcs_serve_create", "lcs_serve_submit",
     "lcs_serve_poll", "lcs_serve_wait", "lcs_result_release", "lcs_serve_destroy", "lcs_ctx_set_profiling",
-    "lcs_ctx_last_profile",
+    "lcs_ctx_last_profile", "lcs_tables", "lcs_tables_dev",
 )
 
 
@@ -75,6 +75,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lcs_serve_destroy": (None, [vp]),
         "lcs_ctx_set_profiling": (ctypes.c_int, [vp, ctypes.c_int]),
         "lcs_ctx_last_profile": (ctypes.c_int, [vp, ctypes.POINTER(Profile)]),
+        "lcs_tables": (ctypes.c_int, [vp, u8p, u64, u8p, u64, ctypes.POINTER(ctypes.c_uint32), u8p]),
+        "lcs_tables_dev": (ctypes.c_int, [vp, vp, u64, vp, u64, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -168,6 +170,17 @@ class Context:
         _check(rc, "lcs_traceback")
         return out[: n_out.value].tobytes()
 
+    def tables(self, x, y) -> tuple[np.ndarray, np.ndarray]:
+        """(c, b) of LCS-length: c of shape (m+1, n+1) uint32, b of shape (m, n) uint8 (1 DIAG, 2 UP, 3 LEFT)."""
+        x, y = _u8(x), _u8(y)
+        m, n = len(x), len(y)
+        c = np.zeros((m + 1) * (n + 1), dtype=np.uint32)
+        b = np.zeros(max(m * n, 1), dtype=np.uint8)
+        rc = _lib.lcs_tables(self._h, _p8(x) if m else None, m, _p8(y) if n else None, n,
+                             c.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), _p8(b))
+        _check(rc, "lcs_tables")
+        return c.reshape(m + 1, n + 1), b[: m * n].reshape(m, n)
+
     def batch(self, pairs) -> np.ndarray:
         xs = [_u8(x) for x, _ in pairs]
         ys = [_u8(y) for _, y in pairs]
@@ -213,6 +226,13 @@ class Context:
                                     y.numel(), ctypes.c_void_p(out.data_ptr()), out.numel(),
                                     ctypes.c_void_p(out_len.data_ptr()), _stream_ptr(stream))
         _check(rc, "lcs_traceback_dev")
+
+    def tables_dev(self, x, y, c, b, stream=None) -> None:
+        """c: int32/uint32 CUDA tensor of (m+1)*(n+1) elements; b: uint8 CUDA tensor of m*n elements."""
+        rc = _lib.lcs_tables_dev(self._h, ctypes.c_void_p(x.data_ptr()), x.numel(), ctypes.c_void_p(y.data_ptr()),
+                                 y.numel(), ctypes.c_void_p(c.data_ptr()), ctypes.c_void_p(b.data_ptr()),
+                                 _stream_ptr(stream))
+        _check(rc, "lcs_tables_dev")
 
     def batch_dev(self, xs, x_off, ys, y_off, count: int, out, stream=None) -> None:
         rc = _lib.lcs_batch_dev(self._h, ctypes.c_void_p(xs.data_ptr()), ctypes.c_void_p(x_off.data_ptr()),

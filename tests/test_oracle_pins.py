@@ -190,3 +190,28 @@ def test_traceback_capacity_error(oracle):
     rc = lib.oracle_lcs_traceback(x.ctypes.data_as(u8), 8, y.ctypes.data_as(u8), 8, out.ctypes.data_as(u8), 2,
                                   ctypes.byref(n_out))
     assert rc == -2 and n_out.value == 5
+
+
+# ----------------------------------------------------------------------------------------------------------------
+# The multi-threaded oracle (column blocks over host threads, §II.A-B) gives the serial oracle's results
+# ----------------------------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("threads", [1, 2, 3, 5, 16])
+def test_parallel_oracle_equals_serial(oracle, threads):
+    rng = np.random.default_rng(31 + threads)
+    for k in range(25):
+        m = int(rng.integers(1, 300))
+        n = int(rng.integers(1, 200))
+        alpha = [b"AB", b"ACGT", bytes(range(20))][k % 3]
+        x = bytes(rng.choice(list(alpha), m).astype(np.uint8))
+        y = bytes(rng.choice(list(alpha), n).astype(np.uint8))
+        assert oracle.lcs_traceback_par(x, y, threads) == oracle.lcs_traceback(x, y), (m, n)
+
+
+def test_parallel_oracle_edges(oracle):
+    assert oracle.lcs_traceback_par(b"", b"ACGT", 4) == b""
+    assert oracle.lcs_traceback_par(b"A", b"A", 8) == b"A"  # more threads than columns
+    x = b"ACGTTGCA" * 40
+    assert oracle.lcs_traceback_par(x, x, 4) == x
+    for x, y, L, s in read_golden_cases(GOLDEN)[0]:
+        assert oracle.lcs_traceback_par(x, y, 3) == s
