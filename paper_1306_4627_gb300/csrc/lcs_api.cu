@@ -221,12 +221,15 @@ int run_traceback(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y
   if (!rc && rev) rc = from_cuda(ensure(c->carry_r, g.nblocks * Rr * 4));
   if (!rc && rev) rc = from_cuda(ensure(c->snap_r, S * g.wpad * 4));
   if (!rc) rc = from_cuda(ensure(c->colsum, (S * 2 * (g.wq + 1) + 4) * 4));
-  if (!rc) rc = from_cuda(ensure(c->ent, S * kWalkers * 4));
-  if (!rc) rc = from_cuda(ensure(c->ext, S * kWalkers * 4));
-  if (!rc) rc = from_cuda(ensure(c->nch, S * kWalkers * 4));
+  // walkers per segment: as many as the corridor can have columns (n + 1), within the budget
+  uint64_t W = std::min<uint64_t>(n + 1, std::min<uint64_t>(kMaxWalkersPerSeg, kWalkerBudget / S));
+  W = std::max<uint64_t>(kWalkers, (W + kWalkers - 1) / kWalkers * kWalkers);
+  if (!rc) rc = from_cuda(ensure(c->ent, S * W * 4));
+  if (!rc) rc = from_cuda(ensure(c->ext, S * W * 4));
+  if (!rc) rc = from_cuda(ensure(c->nch, S * W * 4));
   if (!rc) rc = from_cuda(ensure(c->entcnt, S * 4));
   if (!rc) rc = from_cuda(ensure(c->sel, S * 4));
-  if (!rc) rc = from_cuda(ensure(c->chars, S * (kWalkers + 1) * H));
+  if (!rc) rc = from_cuda(ensure(c->chars, S * (W + 1) * H));
   if (rc) return rc;
   rc = from_cuda(launch_xoff(d_x, m, false, 0, Rf, B, c->codemap(), c->sigma(), (uint32_t*)c->xoff_f.p,
                              (uint8_t*)c->xcode.p, st));
@@ -289,6 +292,7 @@ int run_traceback(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y
   t.H = H;
   t.S = S;
   t.B = B;
+  t.W = (uint32_t)W;
   t.status = c->status();
   rc = from_cuda(launch_traceback(t, st));
   c->mark(3, st);

@@ -60,7 +60,9 @@ struct FillArgs {
 };
 
 // ---- traceback segment walkers ---------------------------------------------------------------------------------
-constexpr int kWalkers = 32;            // walkers per segment (one warp)
+constexpr int kWalkers = 32;            // walkers per warp; a segment has W of them (a multiple of 32)
+constexpr int kMaxWalkersPerSeg = 1024; // W <= this, and S * W <= kWalkerBudget
+constexpr int kWalkerBudget = 65536;
 constexpr int kMaxSegments = 256;
 
 struct TraceArgs {
@@ -71,11 +73,11 @@ struct TraceArgs {
   const uint32_t* snapF;    // forward V snapshots, index k-1 = row k*H
   const uint32_t* snapR;    // reverse V snapshots, index S-k-1 = forward row k*H
   const unsigned long long* L;  // c[m,n]
-  uint32_t* ent;            // [S][kWalkers] entry columns of the walkers
-  uint32_t* ent_cnt;        // [S] walkers per segment (kWalkers+1 = corridor overflow)
-  uint32_t* ext;            // [S][kWalkers] exit columns
-  uint32_t* nch;            // [S][kWalkers] symbols emitted by each walker
-  uint8_t* chars;           // [S][kWalkers + 1][H] emitted symbols in walk order (slot kWalkers: fallback)
+  uint32_t* ent;            // [S][W] entry columns of the walkers
+  uint32_t* ent_cnt;        // [S] corridor columns found (more than W: the segment may need the fallback walk)
+  uint32_t* ext;            // [S][W] exit columns
+  uint32_t* nch;            // [S][W] symbols emitted by each walker
+  uint8_t* chars;           // [S][W + 1][H] emitted symbols in walk order (slot W: the fallback walk)
   uint32_t* sel;            // [S] selected walker per segment
   uint32_t* colsum;         // scratch [2][S][w+1] word prefix popcounts
   uint8_t* out;             // LCS output (capacity out_cap)
@@ -83,6 +85,7 @@ struct TraceArgs {
   uint64_t out_cap;
   uint64_t m, n, w, wpad, R, H, S;
   uint32_t B;
+  uint32_t W;               // walkers per segment
   DevStatus* status;
 };
 

@@ -42,11 +42,12 @@ struct Req {
   bool short_pair = false;
 };
 
-// Device bytes a traceback of an m x n pair holds: the direction bitmap plus its per-row scratch (rounded up).
+// Device bytes a traceback of an m x n pair holds: the direction bitmap plus its per-row scratch and the segment
+// walkers' buffers (at most 65536 walkers of 256-row segments), rounded up.
 uint64_t traceback_bytes(uint64_t m, uint64_t n) {
   const uint64_t words = n / 32 + 1;
   const uint64_t lanes = (words + 127) / 128 * 128;
-  return lanes * ((m + 7) / 8 + 31) * 8 * 4 + (uint64_t)257 * lanes * 8 + 64 * m + (16u << 20);
+  return lanes * ((m + 7) / 8 + 31) * 8 * 4 + (uint64_t)257 * lanes * 8 + 64 * m + (40u << 20);
 }
 
 }  // namespace

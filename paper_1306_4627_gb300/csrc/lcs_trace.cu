@@ -101,7 +101,7 @@ __global__ void k_corr_cols(TraceArgs a) {
     const uint32_t sum = ones_prefix(vf, pf, j) + ones_prefix(vr, pr, a.n - j);
     if (sum == target) {
       const uint32_t slot = atomicAdd(&a.ent_cnt[s], 1u);
-      if (slot < (uint32_t)kWalkers) a.ent[s * kWalkers + slot] = (uint32_t)j;
+      if (slot < a.W) a.ent[s * a.W + slot] = (uint32_t)j;
     }
   }
 }
@@ -187,20 +187,102 @@ __device__ uint64_t walk_segment(const TraceArgs& a, uint64_t hi, uint64_t lo, u
   return j;
 }
 
-__global__ void k_walk(TraceArgs a) {
-  const uint64_t s = blockIdx.x;
-  const uint32_t k = threadIdx.x;
-  const uint32_t cnt = a.ent_cnt[s];
-  if (k >= (cnt < (uint32_t)kWalkers ? cnt : (uint32_t)kWalkers)) return;
-  const uint64_t lo = s * a.H, hi = (s + 1) * a.H < a.m ? (s + 1) * a.H : a.m;
-  const uint64_t e = a.ent[s * kWalkers + k];
-  uint32_t nc = 0;
-  const uint64_t x = walk_segment(a, hi, lo, e, a.chars + (s * (kWalkers + 1) + k) * a.H, &nc);
-  a.ext[s * kWalkers + k] = (uint32_t)x;
-  a.nch[s * kWalkers + k] = nc;
+// The same walk done by a whole warp (all lanes call it with the same arguments and follow the same path): lane k
+// fetches the words of row i - k at the walk's current 32-column word, so the loads of 32 rows overlap, and the
+// walk takes them from the lanes one row at a time. Lane 0 writes the emitted symbols.
+__device__ uint64_t walk_segment_warp(const TraceArgs& a, uint64_t hi, uint64_t lo, uint64_t e, uint8_t* out_chars,
+                                      uint32_t* out_cnt) {
+  const uint32_t lane = threadIdx.x & 31;
+  uint64_t i = hi, j = e;
+  uint32_t cnt = 0;
+  while (i > lo && j > 0) {
+    const int64_t Qg = (int64_t)(j >> 5);
+    const bool ok = i > lo + lane;
+    const uint32_t cd = ok ? a.xcode[i - lane - 1] : 0u;
+    const uint32_t xs = ok ? a.x[i - lane - 1] : 0u;
+    const uint32_t dv = ok ? t_word(a, i - lane, (uint64_t)Qg) : 0u;
+    const uint32_t pa = ok ? p_word(a, cd, Qg) : 0u;
+    const uint32_t pb = ok ? p_word(a, cd, Qg - 1) : 0u;
+    // row k's words are taken from lane k one row ahead of their use
+    uint32_t n_code = __shfl_sync(kFull, cd, 0), n_sym = __shfl_sync(kFull, xs, 0);
+    uint32_t n_dk = __shfl_sync(kFull, dv, 0), n_pak = __shfl_sync(kFull, pa, 0), n_pbk = __shfl_sync(kFull, pb, 0);
+    for (uint32_t k = 0; k < 32; ++k) {
+      if (i <= lo || j == 0) break;  // the same on every lane
+      const uint32_t code = n_code, sym = n_sym, dk = n_dk, pak = n_pak, pbk = n_pbk;
+      const uint32_t kn = (k + 1) & 31;
+      n_code = __shfl_sync(kFull, cd, kn);
+      n_sym = __shfl_sync(kFull, xs, kn);
+      n_dk = __shfl_sync(kFull, dv, kn);
+      n_pak = __shfl_sync(kFull, pa, kn);
+      n_pbk = __shfl_sync(kFull, pb, kn);
+      int64_t Q = (int64_t)(j >> 5);
+      if (Q == Qg) {  // most rows stop at column j itself (an UP or a match there): no bit scan
+        const uint32_t bj = (uint32_t)(j & 31);
+        const uint32_t pmj = (bj ? (pak >> (bj - 1)) : (pbk >> 31)) & 1u;
+        if (((dk >> bj) & 1u) == 0u || pmj) {
+          if (pmj) {
+            if (lane == 0) out_chars[cnt] = (uint8_t)sym;
+            ++cnt;
+            --j;
+          }
+          --i;
+          continue;
+        }
+      }
+      uint32_t mask = kFull >> (31 - (uint32_t)(j & 31));
+      uint32_t pm = 0, stop = 0;
+      for (;;) {
+        uint32_t d;
+        if (Q == Qg) {
+          d = dk;
+          pm = (pak << 1) | (pbk >> 31);
+        } else {
+          d = t_word(a, i, (uint64_t)Q);
+          pm = (p_word(a, code, Q) << 1) | (p_word(a, code, Q - 1) >> 31);
+        }
+        stop = (pm | ~d) & mask;
+        if (Q == 0) stop &= ~1u;
+        if (stop || Q == 0) break;
+        --Q;
+        mask = kFull;
+      }
+      if (!stop) {
+        j = 0;
+        break;
+      }
+      const uint32_t bit = 31u - __clz(stop);
+      const uint64_t c = ((uint64_t)Q << 5) + bit;
+      if ((pm >> bit) & 1u) {
+        if (lane == 0) out_chars[cnt] = (uint8_t)sym;
+        ++cnt;
+        j = c - 1;
+      } else {
+        j = c;
+      }
+      --i;
+    }
+  }
+  *out_cnt = cnt;
+  return j;
 }
 
-// Follows the true path from (m, n) down the segments (one warp; all entries and exits staged in shared memory).
+// Walker k of segment s (block (s, k / 32), thread k % 32) walks from the k-th corridor column found.
+__global__ void k_walk(TraceArgs a) {
+  const uint64_t s = blockIdx.x;
+  const uint32_t k = blockIdx.y * kWalkers + threadIdx.x;
+  const uint32_t cnt = a.ent_cnt[s];
+  if (k >= (cnt < a.W ? cnt : a.W)) return;
+  const uint64_t lo = s * a.H, hi = (s + 1) * a.H < a.m ? (s + 1) * a.H : a.m;
+  const uint64_t e = a.ent[s * a.W + k];
+  uint32_t nc = 0;
+  const uint64_t x = walk_segment(a, hi, lo, e, a.chars + (s * (a.W + 1) + k) * a.H, &nc);
+  a.ext[s * a.W + k] = (uint32_t)x;
+  a.nch[s * a.W + k] = nc;
+}
+
+// Follows the true path from (m, n) down the segments (one warp). The first 32 walkers of every segment are staged
+// in shared memory; a segment whose corridor had more columns is searched in global memory, and when its entry
+// is not among its walkers at all (more corridor columns than W) the warp walks the segment itself.
 __global__ void k_chain(TraceArgs a) {
   extern __shared__ uint32_t sm[];
   uint32_t* ent = sm;                         // [S][kWalkers]
@@ -208,39 +290,47 @@ __global__ void k_chain(TraceArgs a) {
   uint32_t* cnt = sm + 2 * a.S * kWalkers;    // [S]
   const uint32_t lane = threadIdx.x;
   for (uint64_t i = lane; i < a.S * kWalkers; i += 32) {
-    ent[i] = a.ent[i];
-    ext[i] = a.ext[i];
+    const uint64_t src = (i / kWalkers) * a.W + (i % kWalkers);
+    ent[i] = a.ent[src];
+    ext[i] = a.ext[src];
   }
   for (uint64_t i = lane; i < a.S; i += 32) cnt[i] = a.ent_cnt[i];
   __syncwarp();
   uint64_t e = a.n;
   for (int64_t s = (int64_t)a.S - 1; s >= 0; --s) {
-    const uint32_t c = cnt[s] < (uint32_t)kWalkers ? cnt[s] : (uint32_t)kWalkers;
+    const uint32_t c = cnt[s] < a.W ? cnt[s] : a.W;
     const bool hit = lane < c && ent[s * kWalkers + lane] == (uint32_t)e;
-    const uint32_t b = __ballot_sync(kFull, hit);
+    uint32_t b = __ballot_sync(kFull, hit);
+    uint32_t k = b ? (uint32_t)__ffs(b) - 1 : 0u;
+    uint32_t exit_col = b ? ext[s * kWalkers + k] : 0u;
+    for (uint32_t base = kWalkers; !b && base < c; base += kWalkers) {  // a wide corridor
+      const uint32_t q = base + lane;
+      b = __ballot_sync(kFull, q < c && a.ent[(uint64_t)s * a.W + q] == (uint32_t)e);
+      if (b) {
+        k = base + (uint32_t)__ffs(b) - 1;
+        exit_col = a.ext[(uint64_t)s * a.W + k];
+      }
+    }
     if (b) {
-      const uint32_t k = __ffs(b) - 1;
       if (lane == 0) a.sel[s] = k;
-      e = ext[s * kWalkers + k];
+      e = exit_col;
     } else {
-      // the entry is not among the walkers (corridor wider than the warp): walk the segment here
-      uint64_t x = 0;
+      // the entry is not among the walkers (more corridor columns than walkers): the warp walks the segment here
+      const uint64_t lo = (uint64_t)s * a.H, hi = ((uint64_t)s + 1) * a.H < a.m ? ((uint64_t)s + 1) * a.H : a.m;
+      uint32_t nc = 0;
+      e = walk_segment_warp(a, hi, lo, e, a.chars + ((uint64_t)s * (a.W + 1) + a.W) * a.H, &nc);
       if (lane == 0) {
-        const uint64_t lo = (uint64_t)s * a.H, hi = ((uint64_t)s + 1) * a.H < a.m ? ((uint64_t)s + 1) * a.H : a.m;
-        uint32_t nc = 0;
-        x = walk_segment(a, hi, lo, e, a.chars + ((uint64_t)s * (kWalkers + 1) + kWalkers) * a.H, &nc);
-        a.sel[s] = kWalkers;
+        a.sel[s] = a.W;
         a.ent_cnt[s] = 0x80000000u | nc;  // fallback count, read by k_finalize
       }
-      e = __shfl_sync(kFull, x, 0);
     }
   }
 }
 
 __device__ __forceinline__ uint32_t seg_count(const TraceArgs& a, uint64_t s) {
   const uint32_t k = a.sel[s];
-  if (k == (uint32_t)kWalkers) return a.ent_cnt[s] & 0x7FFFFFFFu;
-  return a.nch[s * kWalkers + k];
+  if (k == a.W) return a.ent_cnt[s] & 0x7FFFFFFFu;
+  return a.nch[s * a.W + k];
 }
 
 // Block s copies its selected walker's symbols (walk order = reverse output order) to their place in the output.
@@ -274,7 +364,7 @@ __global__ void k_finalize(TraceArgs a) {
   total = red[16];
   const uint32_t k = a.sel[s];
   const uint32_t c = seg_count(a, s);
-  const uint8_t* src = a.chars + (s * (kWalkers + 1) + k) * a.H;
+  const uint8_t* src = a.chars + (s * (a.W + 1) + k) * a.H;
   const bool fits = (uint64_t)before + c <= a.out_cap;  // always true unless the walks were inconsistent
   if (fits)
     for (uint32_t t = threadIdx.x; t < c; t += blockDim.x) a.out[before + c - 1 - t] = src[t];
@@ -285,7 +375,7 @@ __global__ void k_finalize(TraceArgs a) {
 
 // Segment S-1 starts at (m, n); segments with no boundary corridor data (S == 1) likewise.
 __global__ void k_seed_last(TraceArgs a) {
-  a.ent[(a.S - 1) * kWalkers] = (uint32_t)a.n;
+  a.ent[(a.S - 1) * a.W] = (uint32_t)a.n;
   a.ent_cnt[a.S - 1] = 1;
 }
 
@@ -360,7 +450,7 @@ cudaError_t launch_traceback(const TraceArgs& a, cudaStream_t st) {
     if (gx > 1024) gx = 1024;
     k_corr_cols<<<dim3((unsigned)gx, (unsigned)(a.S - 1)), 256, 0, st>>>(a);
   }
-  k_walk<<<(unsigned)a.S, kWalkers, 0, st>>>(a);
+  k_walk<<<dim3((unsigned)a.S, a.W / kWalkers), kWalkers, 0, st>>>(a);
   const size_t chain_smem = (size_t)(2 * a.S * kWalkers + a.S) * sizeof(uint32_t);
   e = cudaFuncSetAttribute(k_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chain_smem);
   if (e != cudaSuccess) return e;
