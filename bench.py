@@ -441,7 +441,7 @@ def run_serve_workload(args):
     for rate in rates:
         reqs = gen.serve_requests(rate=rate, count=args.serve_count, seed=gen.BASE_SEED + 4)
         cells = sum(len(r["x"]) * len(r["y"]) for r in reqs)
-        srv = lcs.Server(ctx)
+        srv = lcs.Server(ctx, pair_workers=args.pair_workers)
         # warm the workers' buffers with a few requests
         for r in reqs[:8]:
             srv.wait(srv.submit(r["x"], r["y"], traceback=r["traceback"]), timeout_s=60.0)
@@ -486,7 +486,7 @@ def run_serve_workload(args):
         "warmup": 1, "ms_per_step": best["wall_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": "serving: Poisson arrivals, m,n log-uniform [32, 65536], sigma 4/20/256, 20% traceback",
-                   "requests_per_rate": args.serve_count},
+                   "requests_per_rate": args.serve_count, "pair_workers": args.pair_workers or 8},
         "rates": out_rates,
         "per_pair_baseline": {"p50_ms": float(np.percentile(svc, 50) * 1e3), "p99_ms": float(np.percentile(svc, 99) * 1e3),
                               "gcups": sum(len(r["x"]) * len(r["y"]) for r in reqs) / svc.sum() / 1e9,
@@ -582,6 +582,7 @@ def main():
     ap.add_argument("--seq-sample", type=int, default=400, help="pairs timed as sequential single-pair launches")
     ap.add_argument("--rates", default="1000,3000,10000,30000,100000", help="serving: request rates per second")
     ap.add_argument("--serve-count", type=int, default=3000, help="serving: requests per rate")
+    ap.add_argument("--pair-workers", type=int, default=0, help="serving: single-pair workers (0 = the default)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -166,7 +166,7 @@ typedef struct lcs_serve_cfg {
   uint32_t max_batch;          /* short pairs packed into one batched launch (0 = 4096) */
   uint64_t hbm_budget_bytes;   /* device bytes the server may hold for traceback bitmaps (0 = 60% of free) */
   uint32_t long_pair_cells_log2; /* pairs with m*n >= 2^this run on the single-pair path (0 = 2^24) */
-  uint32_t reserved;
+  uint32_t pair_workers;       /* single-pair workers, each with its own stream and buffers (0 = 8, at most 32) */
 } lcs_serve_cfg;
 
 typedef struct lcs_result {

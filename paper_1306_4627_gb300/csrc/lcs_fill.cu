@@ -128,6 +128,8 @@ struct Lane {
   uint32_t cin_b;     // carries for rows B/2 .. B-1
   uint32_t win;       // inbound window of the current 32-step block t0 .. t0+31: slot t0 + lane
   uint32_t win_next;  // the next block's window, requested in the middle of the current block
+  uint32_t cin0;      // the previous warp's carries for this step's row-block (lane 0's input), taken from the
+                      // window one step ahead, or right after a validation at a window or group start
   uint32_t cap;       // V captured at the end of this lane's row-block r with (r + 1) % 32 == 0 in this block
   uint32_t xstage[16];  // symbol offsets of row-block t0 + 34 + lane, staged for the next 32-step boundary
   uint4* tp;          // this step's bitmap chunk of the warp, plus this lane's offset
@@ -204,9 +206,10 @@ __device__ __forceinline__ void fill_step(const Warp& w, Lane& s, int32_t t, con
   p_from_offsets<B>(w, xa, pl);
   xo_from_ring<B>(w, r + 2, xl);
   uint32_t cin0 = 0;
-  if (SRC != kSrcNone) {
-    const uint32_t src = __shfl_sync(kFull, s.win, t & 31);
-    cin0 = t < w.R ? (src & ~kTagMask) : 0u;
+  if (SRC != kSrcNone) {  // slot t was read one step ago; read slot t + 1 now, off the path of this step's rows
+    cin0 = s.cin0;
+    const uint32_t nx = __shfl_sync(kFull, s.win, (t + 1) & 31);
+    s.cin0 = t + 1 < w.R ? (nx & ~kTagMask) : 0u;
   }
   // lane 0 takes the previous warp's carries (rows 0 .. B/2-1 at the top of cin0, then the rest)
   const uint32_t cin_a = lane == 0 ? cin0 : s.cin_a;
@@ -278,12 +281,19 @@ __device__ __forceinline__ uint32_t window_load(const Warp& w, int32_t q) {
   return lds_vol_u32(w.ring_src + ((uint32_t)q & (kRing - 1)) * 4u);
 }
 
+// The previous warp's carries for row-block t from the (validated) window.
+template <int B>
+__device__ __forceinline__ void take_cin0(const Warp& w, Lane& s, int32_t t) {
+  constexpr uint32_t kTagMask = (1u << (32 - B)) - 1u;
+  const uint32_t src = __shfl_sync(kFull, s.win, t & 31);
+  s.cin0 = t < w.R ? (src & ~kTagMask) : 0u;
+}
+
 // Start of a VG-step group at t (t % VG == 0) for a warp fed by a shared-memory ring: lanes t%32 .. t%32+VG-1 of
 // the window load the group's VG slots and the warp waits until all of them have arrived (bounded). A group only
 // needs the producer VG + 31 steps ahead, so neighbouring warps in a block run close together.
 template <int B, int SRC, int VG>
-__device__ __forceinline__ void ring_group_validate(const Warp& w, Lane& s, int32_t t) {
-  if (SRC != kSrcRing) return;
+__device__ __forceinline__ void ring_group_wait(const Warp& w, Lane& s, int32_t t) {
   constexpr uint32_t kTagMask = (1u << (32 - B)) - 1u;
   constexpr uint32_t kSel = 32u - VG;  // lane bits that select the group
   const uint32_t lane = w.lane;
@@ -310,12 +320,18 @@ __device__ __forceinline__ void ring_group_validate(const Warp& w, Lane& s, int3
   }
 }
 
+template <int B, int SRC, int VG>
+__device__ __forceinline__ void ring_group_validate(const Warp& w, Lane& s, int32_t t) {
+  if (SRC != kSrcRing) return;
+  ring_group_wait<B, SRC, VG>(w, s, t);
+  take_cin0<B>(w, s, t);
+}
+
 // Start of the 32-step block t0 for a warp fed by global slots: switch to the window requested in the middle of the
 // last block and make sure every slot this block needs has arrived (all lanes together; a bounded wait in the rare
 // case one has not).
 template <int B, int SRC>
-__device__ __forceinline__ void window_validate(const Warp& w, Lane& s, int32_t t0, bool first) {
-  if (SRC != kSrcGlobal) return;
+__device__ __forceinline__ void window_wait(const Warp& w, Lane& s, int32_t t0, bool first) {
   constexpr uint32_t kTagMask = (1u << (32 - B)) - 1u;
   if (!first) s.win = s.win_next;
   const int32_t q = t0 + (int32_t)w.lane;
@@ -337,6 +353,13 @@ __device__ __forceinline__ void window_validate(const Warp& w, Lane& s, int32_t 
     }
     __nanosleep(32);
   }
+}
+
+template <int B, int SRC>
+__device__ __forceinline__ void window_validate(const Warp& w, Lane& s, int32_t t0, bool first) {
+  if (SRC != kSrcGlobal) return;
+  window_wait<B, SRC>(w, s, t0, first);
+  take_cin0<B>(w, s, t0);
 }
 
 // Work at the start of each 32-step block: publish consumption, honour ring back-pressure.
@@ -469,6 +492,7 @@ __global__ void __launch_bounds__(kFillThreads, 1) k_fill(const __grid_constant_
   w.hands_on = (lane == 31 && !(a.debug_drop && gw == 0)) ? 1u : 0u;
   s.win = 0;
   s.win_next = 0;
+  s.cin0 = 0;
   s.tp = J.T ? reinterpret_cast<uint4*>(J.T + (gw * (J.R + 31)) * 32 * (uint64_t)B) + lane : nullptr;
 
   if (TB && J.T) {

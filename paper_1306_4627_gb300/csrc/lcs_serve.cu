@@ -4,11 +4,13 @@
 // stream), take work as soon as they are free, so requests that arrive while others run join the next launch:
 //   * one batch worker takes every waiting short length-only request (up to max_batch) and runs them as one
 //     persistent batched launch (lcs_batch);
-//   * several single-pair workers take long pairs and all traceback requests, one at a time each (lcs_length /
-//     lcs_traceback), so their work overlaps on the GPU with the batches and with each other.
+//   * several single-pair workers (lcs_serve_cfg.pair_workers) take long pairs and all traceback requests, one at a
+//     time each (lcs_length / lcs_traceback), so their work overlaps on the GPU with the batches and with each
+//     other (a single pair's fill occupies only n / 4096 SMs).
 // A traceback needs a direction bitmap of about m*n/8 bytes: the server admits it only while the bitmaps of the
 // tracebacks in flight fit the HBM budget (it waits otherwise), and refuses one that could never fit at submit.
 // Every result is computed by the same exact kernels as a call on its own, so it does not depend on the mix.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -23,7 +25,8 @@
 
 namespace {
 
-constexpr int kPairWorkers = 4;
+constexpr uint32_t kPairWorkersDefault = 8;
+constexpr uint32_t kPairWorkersMax = 32;
 
 double now_s() {
   using clk = std::chrono::steady_clock;
@@ -171,6 +174,8 @@ extern "C" int lcs_serve_create(lcs_ctx* ctx, const lcs_serve_cfg* cfg, lcs_serv
   if (s->cfg.max_queue == 0) s->cfg.max_queue = 65536;
   if (s->cfg.max_batch == 0) s->cfg.max_batch = 4096;
   if (s->cfg.long_pair_cells_log2 == 0) s->cfg.long_pair_cells_log2 = 24;
+  if (s->cfg.pair_workers == 0) s->cfg.pair_workers = kPairWorkersDefault;
+  s->cfg.pair_workers = std::min(s->cfg.pair_workers, kPairWorkersMax);
   s->long_cells = 1ull << std::min<uint32_t>(s->cfg.long_pair_cells_log2, 62);
   cudaSetDevice(s->device);
   s->budget = s->cfg.hbm_budget_bytes;
@@ -183,7 +188,7 @@ extern "C" int lcs_serve_create(lcs_ctx* ctx, const lcs_serve_cfg* cfg, lcs_serv
     }
     s->budget = (uint64_t)(free_b * 0.6);
   }
-  for (int k = 0; k < 1 + kPairWorkers; ++k) {
+  for (uint32_t k = 0; k < 1 + s->cfg.pair_workers; ++k) {
     lcs_ctx* c = nullptr;
     const int rc = lcs_ctx_create(s->device, &c);
     if (rc) {
@@ -194,7 +199,8 @@ extern "C" int lcs_serve_create(lcs_ctx* ctx, const lcs_serve_cfg* cfg, lcs_serv
     s->ctxs.push_back(c);
   }
   s->threads.emplace_back(&lcs_server::batch_worker, s, s->ctxs[0]);
-  for (int k = 0; k < kPairWorkers; ++k) s->threads.emplace_back(&lcs_server::pair_worker, s, s->ctxs[1 + k]);
+  for (uint32_t k = 0; k < s->cfg.pair_workers; ++k)
+    s->threads.emplace_back(&lcs_server::pair_worker, s, s->ctxs[1 + k]);
   *out = s;
   return LCS_OK;
 }

@@ -36,7 +36,7 @@ class LCSError(RuntimeError):
 
 class ServeCfg(ctypes.Structure):
     _fields_ = [("max_queue", ctypes.c_uint32), ("max_batch", ctypes.c_uint32), ("hbm_budget_bytes", ctypes.c_uint64),
-                ("long_pair_cells_log2", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("long_pair_cells_log2", ctypes.c_uint32), ("pair_workers", ctypes.c_uint32)]
 
 
 class Profile(ctypes.Structure):
@@ -245,8 +245,8 @@ class Server:
     """lcs_server: continuous batching of requests submitted over time."""
 
     def __init__(self, ctx: Context, max_queue: int = 0, max_batch: int = 0, hbm_budget_bytes: int = 0,
-                 long_pair_cells_log2: int = 0):
-        cfg = ServeCfg(max_queue, max_batch, hbm_budget_bytes, long_pair_cells_log2, 0)
+                 long_pair_cells_log2: int = 0, pair_workers: int = 0):
+        cfg = ServeCfg(max_queue, max_batch, hbm_budget_bytes, long_pair_cells_log2, pair_workers)
         h = ctypes.c_void_p()
         _check(_lib.lcs_serve_create(ctx.handle, ctypes.byref(cfg), ctypes.byref(h)), "lcs_serve_create")
         self._h = h
