@@ -187,6 +187,9 @@ def run_gpu(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)
     ctx = lcs.Context(local)
     stream = torch.cuda.Stream(device=dev)
+    tuned = None
+    if not args.no_autotune:  # the library's autotuner picks the fill configuration on this pair, before timing
+        tuned = ctx.autotune_dev(x, y, traceback=True, stream=stream)
     ctx.set_profiling(True)
 
     def step():
@@ -280,6 +283,7 @@ def run_gpu(args):
                 "d2h_bytes_per_step": 8 + L},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
+        "fill_config": tuned or ctx.get_fill_config(traceback=True),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -576,6 +580,7 @@ def main():
     ap.add_argument("--m", type=int, default=M, help="rows (profiling of smaller cases only)")
     ap.add_argument("--n", type=int, default=N, help="columns (profiling of smaller cases only)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default fill configuration")
     ap.add_argument("--workload", default="pair", choices=["pair", "batch", "long", "serve", "table1"],
                     help="pair: the 65536^2 traceback step (default); batch: 10000 pairs; long: 262144^2 length; "
                          "serve: Poisson request streams; table1: the shapes of the paper's Table 1")

@@ -86,6 +86,27 @@ LCS_API int lcs_ctx_set_profiling(lcs_ctx* ctx, int enable);
  * profiled yet. */
 LCS_API int lcs_ctx_last_profile(lcs_ctx* ctx, lcs_profile* out);
 
+/* ---- fill configuration (no counterpart in the paper: how the table fill of §I.C is laid out on the GPU) -------- */
+
+/* rows_per_step: rows of the table one systolic step of the fill covers (8 or 16); vg_select: 0 = the default
+ * hand-off validation group of the fill's warps, 1 = the alternative (32 steps at 8 rows, 16 at 16 rows). Every
+ * configuration gives the same results; only the time differs. mode 0 = length-only calls, 1 = traceback calls
+ * (lcs_traceback*, lcs_tables*). */
+typedef struct lcs_fill_config {
+  uint32_t rows_per_step;
+  uint32_t vg_select;
+} lcs_fill_config;
+
+LCS_API int lcs_ctx_get_fill_config(lcs_ctx* ctx, uint32_t mode, lcs_fill_config* out);
+LCS_API int lcs_ctx_set_fill_config(lcs_ctx* ctx, uint32_t mode, const lcs_fill_config* cfg);
+
+/* Autotuner: times every configuration on the device pair (d_x, m, d_y, n) in the given mode (one untimed and
+ * three timed calls each, events on `stream`), keeps the fastest in the context for that mode and returns it in
+ * *best with its median time in *best_ms (either may be NULL). Blocking. The caller may store the result and set
+ * it on later contexts with lcs_ctx_set_fill_config. */
+LCS_API int lcs_ctx_autotune_dev(lcs_ctx* ctx, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, uint64_t n,
+                                 uint32_t mode, void* stream, lcs_fill_config* best, double* best_ms);
+
 /* ---- length (paper §I.C, LCS-length; returns c[m,n]) --------------------------------------------------------- */
 
 /* Host buffers x[0..m), y[0..n); writes c[m,n] to *out_len. Blocking. m = 0 or n = 0 gives 0. Errors:

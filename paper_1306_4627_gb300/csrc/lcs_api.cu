@@ -76,7 +76,7 @@ int run_fill(lcs_ctx* c, FillJob* jobs, int njobs, bool traceback, uint32_t B, c
   FillArgs a{};
   a.status = c->status();
   a.spin_limit = c->spin_limit;
-  a.variant = c->fill_variant;
+  a.variant = traceback ? c->fill_variant_tb : c->fill_variant;
   a.debug_drop = c->debug_drop;
   uint32_t total = 0;
   for (int k = 0; k < njobs; ++k) total += jobs[k].nblocks_total;
@@ -377,7 +377,7 @@ extern "C" int lcs_ctx_create(int device, lcs_ctx** out) {
     return rc;
   }
   if (const char* e = getenv("LCS_FILL_B")) c->fill_B = c->fill_B_tb = (atoi(e) == 16) ? 16u : 8u;
-  if (const char* e = getenv("LCS_FILL_VARIANT")) c->fill_variant = (uint32_t)atoi(e);
+  if (const char* e = getenv("LCS_FILL_VARIANT")) c->fill_variant = c->fill_variant_tb = (uint32_t)atoi(e);
   // bounded-wait testing: a short wait limit and a carry hand-off that is never published
   if (const char* e = getenv("LCS_SPIN_LIMIT")) c->spin_limit = (uint32_t)std::max(64, atoi(e));
   if (const char* e = getenv("LCS_DEBUG_DROP_HANDOFF")) c->debug_drop = atoi(e) ? 1u : 0u;
@@ -555,4 +555,92 @@ extern "C" int lcs_tables(lcs_ctx* c, const uint8_t* x, uint64_t m, const uint8_
   if (dc) cudaFree(dc);
   if (db) cudaFree(db);
   return rc;
+}
+
+// ---- fill configuration and autotuning -------------------------------------------------------------------------
+
+static bool valid_fill_config(const lcs_fill_config* f) {
+  return f && (f->rows_per_step == 8 || f->rows_per_step == 16) && f->vg_select <= 1;
+}
+
+extern "C" int lcs_ctx_get_fill_config(lcs_ctx* c, uint32_t mode, lcs_fill_config* out) {
+  if (!c || !out || mode > 1) return LCS_ERR_INVALID;
+  std::lock_guard<std::mutex> g(c->mu);
+  out->rows_per_step = mode ? c->fill_B_tb : c->fill_B;
+  out->vg_select = (((mode ? c->fill_variant_tb : c->fill_variant) >> 1) & 3u) == 2u ? 1u : 0u;
+  return LCS_OK;
+}
+
+static void apply_fill_config(lcs_ctx* c, uint32_t mode, const lcs_fill_config* f) {
+  const uint32_t var = f->vg_select ? 4u : 0u;  // bits 1-2 = 2: the alternative validation group
+  if (mode) {
+    c->fill_B_tb = f->rows_per_step;
+    c->fill_variant_tb = var;
+  } else {
+    c->fill_B = f->rows_per_step;
+    c->fill_variant = var;
+  }
+}
+
+extern "C" int lcs_ctx_set_fill_config(lcs_ctx* c, uint32_t mode, const lcs_fill_config* cfg) {
+  if (!c || mode > 1 || !valid_fill_config(cfg)) return LCS_ERR_INVALID;
+  std::lock_guard<std::mutex> g(c->mu);
+  apply_fill_config(c, mode, cfg);
+  return LCS_OK;
+}
+
+// Times every fill configuration on the caller's pair (one untimed call, then the median of three timed calls, each
+// bracketed by events on the stream), keeps the fastest for the mode and reports it. Results do not depend on the
+// configuration; only the time does.
+extern "C" int lcs_ctx_autotune_dev(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, uint64_t n,
+                                    uint32_t mode, void* stream, lcs_fill_config* best, double* best_ms) {
+  if (!c || mode > 1 || (m && !d_x) || (n && !d_y)) return LCS_ERR_INVALID;
+  if (m >= (1ull << 32) || n >= (1ull << 32)) return LCS_ERR_INVALID;
+  std::lock_guard<std::mutex> g(c->mu);
+  cudaSetDevice(c->device);
+  cudaStream_t st = pick(c, stream);
+  const lcs_fill_config cand[4] = {{8, 0}, {8, 1}, {16, 0}, {16, 1}};
+  lcs_fill_config keep{};
+  keep.rows_per_step = mode ? c->fill_B_tb : c->fill_B;
+  keep.vg_select = (((mode ? c->fill_variant_tb : c->fill_variant) >> 1) & 3u) == 2u ? 1u : 0u;
+  const bool prof = c->prof;
+  c->prof = false;
+  const uint64_t cap = std::max<uint64_t>(std::min(m, n), 1);
+  int rc = mode ? from_cuda(ensure(c->out, cap)) : LCS_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (!rc) rc = from_cuda(cudaEventCreate(&e0));
+  if (!rc) rc = from_cuda(cudaEventCreate(&e1));
+  double bt = 1e300;
+  lcs_fill_config bc = keep;
+  for (const lcs_fill_config& f : cand) {
+    if (rc) break;
+    apply_fill_config(c, mode, &f);
+    double ts[4];
+    for (int k = 0; k < 4 && !rc; ++k) {
+      rc = from_cuda(cudaEventRecord(e0, st));
+      if (!rc)
+        rc = mode ? run_traceback(c, d_x, m, d_y, n, (uint8_t*)c->out.p, cap, c->out_len(), st)
+                  : run_length(c, d_x, m, d_y, n, c->out_len(), st);
+      if (!rc) rc = from_cuda(cudaEventRecord(e1, st));
+      if (!rc) rc = from_cuda(cudaEventSynchronize(e1));
+      if (!rc) rc = take_status(c);
+      float ms = 0.f;
+      if (!rc) rc = from_cuda(cudaEventElapsedTime(&ms, e0, e1));
+      ts[k] = ms;
+    }
+    if (rc) break;
+    std::sort(ts + 1, ts + 4);
+    if (ts[2] < bt) {
+      bt = ts[2];
+      bc = f;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  c->prof = prof;
+  apply_fill_config(c, mode, rc ? &keep : &bc);
+  if (rc) return rc;
+  if (best) *best = bc;
+  if (best_ms) *best_ms = bt;
+  return LCS_OK;
 }

@@ -227,11 +227,24 @@ __global__ void __launch_bounds__(256, 4) k_batch_prep(BatchArgs a) {
       if (lane < 16 && i < pr.mt) xc[i] = map[x[i]];
       xc[(int)lane - (int)kCodePadFront] = (uint16_t)sigma;  // kCodePadFront == 32
       if (lane < kCodePadBack) xc[pr.mt + lane] = (uint16_t)sigma;
-      if (pr.mt < pr.m) {
+      if (pr.mt < pr.m) {  // x[mt + k'] is row rr - 1 - k' of the reverse job; 16-byte loads, 2-byte stores
         uint16_t* xr = a.xcode + pr.xcr;
         const uint32_t rr = pr.m - pr.mt;
-#pragma unroll 4
-        for (uint32_t k = lane; k < rr; k += 32) xr[k] = map[x[pr.m - 1 - k]];
+        const uint8_t* xb = x + pr.mt;
+        const uint32_t rh0 = (uint32_t)((16u - ((uintptr_t)xb & 15u)) & 15u);
+        const uint32_t rh = rh0 < rr ? rh0 : rr;
+        const uint32_t rv = (rr - rh) >> 4;
+        if (lane < rh) xr[rr - 1 - lane] = map[xb[lane]];
+#pragma unroll 2
+        for (uint32_t v = lane; v < rv; v += 32) {
+          const uint4 q = __ldg(reinterpret_cast<const uint4*>(xb + rh + 16 * v));
+          const uint32_t in[4] = {q.x, q.y, q.z, q.w};
+          uint16_t* dst = xr + (rr - 1 - rh - 16 * v);  // rows dst[0], dst[-1], ..., dst[-15]
+#pragma unroll
+          for (int k = 0; k < 16; ++k) dst[-k] = map[(in[k >> 2] >> (8 * (k & 3))) & 0xFF];
+        }
+        const uint32_t kt = rh + 16 * rv + lane;
+        if (lane < 16 && kt < rr) xr[rr - 1 - kt] = map[xb[kt]];
         xr[(int)lane - (int)kCodePadFront] = (uint16_t)sigma;
         if (lane < kCodePadBack) xr[rr + lane] = (uint16_t)sigma;
       }

@@ -37,7 +37,8 @@ struct lcs_ctx {
   uint32_t spin_limit = 1u << 22;
   uint32_t fill_B = 8;        // rows per systolic step of length-only fills (8 or 16)
   uint32_t fill_B_tb = 8;     // rows per systolic step of traceback fills
-  uint32_t fill_variant = 0;  // bit 0: shorter dependent chain per row
+  uint32_t fill_variant = 0;     // length-only fills: bits 1-2 select the hand-off validation group (see launch_fill)
+  uint32_t fill_variant_tb = 0;  // the same for traceback fills
   uint32_t debug_drop = 0;    // test hook (environment LCS_DEBUG_DROP_HANDOFF): a hand-off that never comes
   std::mutex mu;
   lcs::DBuf small, x, y, out;

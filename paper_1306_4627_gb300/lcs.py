@@ -24,7 +24,8 @@ EXPORTS = (
     "lcs_strerror", "lcs_ctx_create", "lcs_ctx_destroy", "lcs_ctx_sync", "lcs_length", "lcs_length_dev",
     "lcs_traceback", "lcs_traceback_dev", "lcs_batch", "lcs_batch_dev", "lcs_serve_create", "lcs_serve_submit",
     "lcs_serve_poll", "lcs_serve_wait", "lcs_result_release", "lcs_serve_destroy", "lcs_ctx_set_profiling",
-    "lcs_ctx_last_profile", "lcs_tables", "lcs_tables_dev",
+    "lcs_ctx_last_profile", "lcs_tables", "lcs_tables_dev", "lcs_ctx_get_fill_config", "lcs_ctx_set_fill_config",
+    "lcs_ctx_autotune_dev",
 )
 
 
@@ -42,6 +43,10 @@ class ServeCfg(ctypes.Structure):
 class Profile(ctypes.Structure):
     _fields_ = [("prep_ms", ctypes.c_double), ("fill_ms", ctypes.c_double), ("trace_ms", ctypes.c_double),
                 ("total_ms", ctypes.c_double), ("fill_blocks", ctypes.c_uint64), ("cells", ctypes.c_uint64)]
+
+
+class FillConfig(ctypes.Structure):
+    _fields_ = [("rows_per_step", ctypes.c_uint32), ("vg_select", ctypes.c_uint32)]
 
 
 class Result(ctypes.Structure):
@@ -77,6 +82,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lcs_ctx_last_profile": (ctypes.c_int, [vp, ctypes.POINTER(Profile)]),
         "lcs_tables": (ctypes.c_int, [vp, u8p, u64, u8p, u64, ctypes.POINTER(ctypes.c_uint32), u8p]),
         "lcs_tables_dev": (ctypes.c_int, [vp, vp, u64, vp, u64, vp, vp, vp]),
+        "lcs_ctx_get_fill_config": (ctypes.c_int, [vp, u32, ctypes.POINTER(FillConfig)]),
+        "lcs_ctx_set_fill_config": (ctypes.c_int, [vp, u32, ctypes.POINTER(FillConfig)]),
+        "lcs_ctx_autotune_dev": (ctypes.c_int, [vp, vp, u64, vp, u64, u32, vp, ctypes.POINTER(FillConfig),
+                                                 ctypes.POINTER(ctypes.c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -153,6 +162,25 @@ class Context:
         p = Profile()
         _check(_lib.lcs_ctx_last_profile(self._h, ctypes.byref(p)), "lcs_ctx_last_profile")
         return {k: getattr(p, k) for k, _ in Profile._fields_}
+
+    def get_fill_config(self, traceback: bool = False) -> dict:
+        f = FillConfig()
+        _check(_lib.lcs_ctx_get_fill_config(self._h, 1 if traceback else 0, ctypes.byref(f)), "lcs_ctx_get_fill_config")
+        return {"rows_per_step": f.rows_per_step, "vg_select": f.vg_select}
+
+    def set_fill_config(self, rows_per_step: int, vg_select: int = 0, traceback: bool = False) -> None:
+        f = FillConfig(rows_per_step, vg_select)
+        _check(_lib.lcs_ctx_set_fill_config(self._h, 1 if traceback else 0, ctypes.byref(f)), "lcs_ctx_set_fill_config")
+
+    def autotune_dev(self, x, y, traceback: bool = False, stream=None) -> dict:
+        """Times every fill configuration on the CUDA tensors x, y and keeps the fastest (lcs_ctx_autotune_dev)."""
+        f = FillConfig()
+        ms = ctypes.c_double(0.0)
+        rc = _lib.lcs_ctx_autotune_dev(self._h, ctypes.c_void_p(x.data_ptr()), x.numel(), ctypes.c_void_p(y.data_ptr()),
+                                       y.numel(), 1 if traceback else 0, _stream_ptr(stream), ctypes.byref(f),
+                                       ctypes.byref(ms))
+        _check(rc, "lcs_ctx_autotune_dev")
+        return {"rows_per_step": f.rows_per_step, "vg_select": f.vg_select, "ms": ms.value}
 
     # -- host buffers -------------------------------------------------------------------------------------------
     def length(self, x, y) -> int:
