@@ -67,8 +67,9 @@ struct BatchArgs {
   uint32_t* peq;
   uint32_t* fvbuf;     // final rows of split pairs' jobs, kWarpWords words per slot
   uint64_t* out_lens;
-  uint32_t* ticket;
+  uint32_t* ticket;      // ticket[0]: items of k_batch_main, ticket[1]: pairs of k_batch_prep
   const uint32_t* split;  // plan indices of split pairs
+  const uint32_t* prep_order;  // plan indices of all pairs, most prep work first
   uint32_t npairs, nitems, nsplit;
 };
 
@@ -82,19 +83,20 @@ constexpr uint32_t kCodePadFront = 32;  // zero-row codes before a job's list: l
 constexpr uint32_t kCodePadBack = 8;    // and after it: the main kernel reads 8 rows at a time
 constexpr uint32_t kCodeZeros = 48;     // zeros at the start of xcode, read by lanes without a job (rows 0..39)
 
-// One match-mask table (see the comment in k_batch_prep): column j of the table reads y[j], or y[n - 1 - j] for
-// the table over reversed y.
+// One match-mask table (see the comment in k_batch_prep): column j of the table has the code ycode[j], or
+// ycode[n - 1 - j] for the table over reversed y. The words are independent; four are in flight at a time.
 template <int NB>
-__device__ __forceinline__ void build_table(uint32_t* tab, const BPair& pr, bool reversed, const uint16_t* map,
-                                            const uint8_t* ysh, uint32_t sigma, uint32_t lane) {
+__device__ __forceinline__ void build_table(uint32_t* tab, const BPair& pr, bool reversed, const uint8_t* ycode,
+                                            uint32_t sigma, uint32_t lane) {
   uint32_t flip0[NB];  // for row r = lane: 0 where bit b of r is set, all ones where it is not
 #pragma unroll
   for (int b = 0; b < NB; ++b) flip0[b] = ((lane >> b) & 1u) - 1u;
+#pragma unroll 4
   for (uint32_t q = 0; q < pr.w; ++q) {
     const uint32_t j = q * 32 + lane;
     const bool in = j < pr.n;
     const uint32_t valid = __ballot_sync(kFull, in);
-    const uint32_t code = in ? map[ysh[reversed ? pr.n - 1 - j : j]] : 0u;
+    const uint32_t code = in ? ycode[reversed ? pr.n - 1 - j : j] : 0u;
     uint32_t pf[NB];
 #pragma unroll
     for (int b = 0; b < NB; ++b) pf[b] = __ballot_sync(kFull, (code >> b) & 1u);
@@ -114,10 +116,10 @@ __device__ __forceinline__ void build_table(uint32_t* tab, const BPair& pr, bool
 }
 
 template <int NB>
-__device__ __noinline__ void build_tables(const BatchArgs& a, const BPair& pr, const uint16_t* map,
-                                          const uint8_t* ysh, uint32_t sigma, uint32_t lane) {
-  build_table<NB>(a.peq + pr.peq_off, pr, false, map, ysh, sigma, lane);
-  if (pr.mt < pr.m) build_table<NB>(a.peq + pr.peqr_off, pr, true, map, ysh, sigma, lane);
+__device__ __noinline__ void build_tables(const BatchArgs& a, const BPair& pr, const uint8_t* ycode, uint32_t sigma,
+                                          uint32_t lane) {
+  build_table<NB>(a.peq + pr.peq_off, pr, false, ycode, sigma, lane);
+  if (pr.mt < pr.m) build_table<NB>(a.peq + pr.peqr_off, pr, true, ycode, sigma, lane);
 }
 
 __global__ void __launch_bounds__(256, 4) k_batch_prep(BatchArgs a) {
@@ -127,8 +129,12 @@ __global__ void __launch_bounds__(256, 4) k_batch_prep(BatchArgs a) {
   const uint32_t wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t* pres = pres_s[wid];
   uint16_t* map = map_s[wid];
-  const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
-  for (uint32_t p = blockIdx.x * (blockDim.x >> 5) + wid; p < a.npairs; p += nwarps) {
+  for (;;) {  // persistent: every warp takes the next pair (most work first) from a ticket
+    uint32_t it = 0;
+    if (lane == 0) it = atomicAdd(a.ticket + 1, 1u);
+    it = __shfl_sync(kFull, it, 0);
+    if (it >= a.npairs) break;
+    const uint32_t p = a.prep_order[it];
     const BPair pr = a.pairs[p];
     // y into shared memory: y[j] at ysh[j], where ysh = y_s + sh places the 16-byte groups of y on 16-byte
     // boundaries of y_s (sh = 16 - (y mod 16), or 0 when y is aligned)
@@ -199,6 +205,9 @@ __global__ void __launch_bounds__(256, 4) k_batch_prep(BatchArgs a) {
     }
     if (lane == 0) a.sigma[p] = sigma;
     __syncwarp();
+    // y's bytes become their codes in place (the codes of y's columns are below sigma <= 256, so they fit a byte)
+    for (uint32_t j = lane; j < pr.n; j += 32) ysh[j] = (uint8_t)map[ysh[j]];
+    __syncwarp();
     // codes of the forward job's rows x[0..mt), 16 symbols per load where the alignment of x allows, then of the
     // reverse job's rows x[m-1] down to x[mt]; each list has kCodePadFront zero-row codes before it and
     // kCodePadBack after it, so the main kernel reads the codes of 8 rows without a bounds check
@@ -255,15 +264,15 @@ __global__ void __launch_bounds__(256, 4) k_batch_prep(BatchArgs a) {
     // per pass); row sigma matches no column, since the columns' codes are 0..sigma-1, and comes out zero.
     const uint32_t nb = 32 - __clz(sigma);  // bits of the codes 0..sigma
     switch (nb) {
-      case 1: build_tables<1>(a, pr, map, ysh, sigma, lane); break;
-      case 2: build_tables<2>(a, pr, map, ysh, sigma, lane); break;
-      case 3: build_tables<3>(a, pr, map, ysh, sigma, lane); break;
-      case 4: build_tables<4>(a, pr, map, ysh, sigma, lane); break;
-      case 5: build_tables<5>(a, pr, map, ysh, sigma, lane); break;
-      case 6: build_tables<6>(a, pr, map, ysh, sigma, lane); break;
-      case 7: build_tables<7>(a, pr, map, ysh, sigma, lane); break;
-      case 8: build_tables<8>(a, pr, map, ysh, sigma, lane); break;
-      default: build_tables<9>(a, pr, map, ysh, sigma, lane); break;
+      case 1: build_tables<1>(a, pr, ysh, sigma, lane); break;
+      case 2: build_tables<2>(a, pr, ysh, sigma, lane); break;
+      case 3: build_tables<3>(a, pr, ysh, sigma, lane); break;
+      case 4: build_tables<4>(a, pr, ysh, sigma, lane); break;
+      case 5: build_tables<5>(a, pr, ysh, sigma, lane); break;
+      case 6: build_tables<6>(a, pr, ysh, sigma, lane); break;
+      case 7: build_tables<7>(a, pr, ysh, sigma, lane); break;
+      case 8: build_tables<8>(a, pr, ysh, sigma, lane); break;
+      default: build_tables<9>(a, pr, ysh, sigma, lane); break;
     }
     __syncwarp();
   }
@@ -452,6 +461,7 @@ struct Plan {
   std::vector<BJob> jobs;
   std::vector<BItem> items;
   std::vector<uint32_t> split;  // plan indices of split pairs
+  std::vector<uint32_t> prep_order;  // plan indices, most prep work first
   uint64_t peq_words = 0;
   uint64_t codes = kCodeZeros;  // xcode: zeros, then the jobs' padded code lists
   uint32_t fv_slots = 0;
@@ -509,6 +519,15 @@ bool make_plan(const uint64_t* x_off, const uint64_t* y_off, uint64_t count, uin
     plan.jobs.push_back({idx, 0u, p.mt, 0u});
     if (split) plan.jobs.push_back({idx, 1u, p.m - p.mt, 0u});
   }
+  // prep order: the table build (n columns, twice for split pairs) dominates a pair's prep
+  plan.prep_order.resize(plan.pairs.size());
+  std::iota(plan.prep_order.begin(), plan.prep_order.end(), 0u);
+  auto prep_cost = [&](uint32_t k) {
+    const BPair& q = plan.pairs[k];
+    return (uint64_t)q.n * (q.mt < q.m ? 2 : 1) + q.m / 16;
+  };
+  std::stable_sort(plan.prep_order.begin(), plan.prep_order.end(),
+                   [&](uint32_t u, uint32_t v) { return prep_cost(u) > prep_cost(v); });
   // bucket jobs by G; within a bucket, longest first (similar rows share a warp)
   std::vector<uint32_t> G(plan.jobs.size());
   for (size_t j = 0; j < plan.jobs.size(); ++j) G[j] = group_lanes(plan.pairs[plan.jobs[j].pair].w);
@@ -552,11 +571,14 @@ static void batch_launches(lcs_ctx* c, uint64_t* d_out, uint64_t count, const Ba
   if (marks) c->mark(0, st);
   cudaMemsetAsync(d_out, 0, count * sizeof(uint64_t), st);  // empty pairs: length 0
   if (a.npairs) {
-    cudaMemsetAsync(a.ticket, 0, 4, st);
+    cudaMemsetAsync(a.ticket, 0, 8, st);
     cudaMemsetAsync(a.xcode, 0, kCodeZeros * sizeof(uint16_t), st);
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-    const unsigned prep_blocks = (unsigned)std::min<uint64_t>((a.npairs + 7) / 8, (uint64_t)sms * 8);
+    int prep_per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&prep_per_sm, k_batch_prep, 256, 0);
+    const unsigned prep_blocks =
+        (unsigned)std::min<uint64_t>((a.npairs + 7) / 8, (uint64_t)sms * std::max(prep_per_sm, 1));
     k_batch_prep<<<prep_blocks, 256, 0, st>>>(a);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_main, kBatchWarps * 32, 0);
     const unsigned blocks = (unsigned)std::max(1, sms * std::max(per_sm, 1));
@@ -597,11 +619,12 @@ int run_batch(lcs_ctx* c, const uint8_t* d_xs, const uint8_t* d_ys, const uint64
     c->bcells = 0;
     for (uint64_t k = 0; k < count; ++k) c->bcells += (x_off[k + 1] - x_off[k]) * (y_off[k + 1] - y_off[k]);
     const size_t pb = plan.pairs.size() * sizeof(BPair), jb = plan.jobs.size() * sizeof(BJob),
-                 ib = plan.items.size() * sizeof(BItem), sb = plan.split.size() * 4;
+                 ib = plan.items.size() * sizeof(BItem), sb = plan.split.size() * 4,
+                 ob = plan.prep_order.size() * 4;
     const size_t jat = (pb + 255) & ~(size_t)255, iat = (jat + jb + 255) & ~(size_t)255,
-                 sat = (iat + ib + 255) & ~(size_t)255;
+                 sat = (iat + ib + 255) & ~(size_t)255, oat = (sat + sb + 255) & ~(size_t)255;
     if (!plan.pairs.empty()) {
-      rc = from_cuda(ensure(c->bplan, sat + sb + 256));
+      rc = from_cuda(ensure(c->bplan, oat + ob + 256));
       if (!rc) rc = from_cuda(ensure(c->bsig, plan.pairs.size() * 4 + 4));
       if (!rc) rc = from_cuda(ensure(c->bxcode, (plan.codes + 16) * 2));
       if (!rc) rc = from_cuda(ensure(c->bpeq, plan.peq_words * 4 + 4));
@@ -613,6 +636,7 @@ int run_batch(lcs_ctx* c, const uint8_t* d_xs, const uint8_t* d_ys, const uint64
       if (!rc) rc = from_cuda(cudaMemcpyAsync(base + jat, plan.jobs.data(), jb, cudaMemcpyHostToDevice, st));
       if (!rc) rc = from_cuda(cudaMemcpyAsync(base + iat, plan.items.data(), ib, cudaMemcpyHostToDevice, st));
       if (!rc && sb) rc = from_cuda(cudaMemcpyAsync(base + sat, plan.split.data(), sb, cudaMemcpyHostToDevice, st));
+      if (!rc) rc = from_cuda(cudaMemcpyAsync(base + oat, plan.prep_order.data(), ob, cudaMemcpyHostToDevice, st));
       if (rc) return rc;
     }
     c->bnpairs = plan.pairs.size();
@@ -621,6 +645,7 @@ int run_batch(lcs_ctx* c, const uint8_t* d_xs, const uint8_t* d_ys, const uint64
     c->bjobs_at = jat;
     c->bitems_at = iat;
     c->bsplit_at = sat;
+    c->border_at = oat;
     std::memcpy(c->bptrs, ptrs, sizeof(ptrs));
     c->boffs.resize(2 * (count + 1));
     for (uint64_t k = 0; k <= count; ++k) {
@@ -636,6 +661,7 @@ int run_batch(lcs_ctx* c, const uint8_t* d_xs, const uint8_t* d_ys, const uint64
   a.jobs = (const BJob*)((char*)c->bplan.p + c->bjobs_at);
   a.items = (const BItem*)((char*)c->bplan.p + c->bitems_at);
   a.split = (const uint32_t*)((char*)c->bplan.p + c->bsplit_at);
+  a.prep_order = (const uint32_t*)((char*)c->bplan.p + c->border_at);
   a.fvbuf = (uint32_t*)c->bfv.p;
   a.sigma = (uint32_t*)c->bsig.p;
   // xcode + xcf is then a multiple of 32 bytes where xs + x_off is a multiple of 16

@@ -25,7 +25,7 @@ constexpr size_t kOffSigma = 544;      // uint32_t
 constexpr size_t kOffLenAcc = 552;     // unsigned long long
 constexpr size_t kOffStatus = 576;     // DevStatus (16 B)
 constexpr size_t kOffOutLen = 608;     // uint64_t
-constexpr size_t kOffTicket = 640;     // uint32_t work ticket of the persistent batch kernel
+constexpr size_t kOffTicket = 640;     // uint32_t[2] work tickets of the persistent batch kernels
 constexpr size_t kSmallBytes = 1024;
 
 }  // namespace lcs
@@ -52,7 +52,7 @@ struct lcs_ctx {
   cudaGraphExec_t bexec = nullptr;
   std::vector<uint64_t> bbig;
   uint64_t bcells = 0, bblocks = 0, bnpairs = 0, bnitems = 0, bnsplit = 0;
-  uint64_t bjobs_at = 0, bitems_at = 0, bsplit_at = 0;  // byte offsets of the plan's parts in bplan
+  uint64_t bjobs_at = 0, bitems_at = 0, bsplit_at = 0, border_at = 0;  // byte offsets of the plan's parts in bplan
   cudaStream_t cap_stream = nullptr;
   uint64_t host_word[1] = {0};
   // stage events of the last profiled call: [0] start, [1] fill start, [2] fill end, [3] end
