@@ -381,6 +381,7 @@ extern "C" int lcs_ctx_create(int device, lcs_ctx** out) {
   // bounded-wait testing: a short wait limit and a carry hand-off that is never published
   if (const char* e = getenv("LCS_SPIN_LIMIT")) c->spin_limit = (uint32_t)std::max(64, atoi(e));
   if (const char* e = getenv("LCS_DEBUG_DROP_HANDOFF")) c->debug_drop = atoi(e) ? 1u : 0u;
+  if (const char* e = getenv("LCS_BATCH_BLOCKS_PER_SM")) c->batch_blocks_per_sm = atoi(e);
   *out = c;
   return LCS_OK;
 }
