@@ -60,6 +60,22 @@ void release(DBuf& b) {
   b.cap = 0;
 }
 
+// Copies the status word and the result length of the call just enqueued on the context's stream back in one
+// transfer, waits for the stream, and returns the latched error (clearing it) or LCS_OK with *len.
+int fetch_result(lcs_ctx* c, uint64_t* len) {
+  static_assert(kOffOutLen > kOffStatus && kOffOutLen - kOffStatus + 8 <= sizeof(c->host_tail), "layout");
+  int rc = from_cuda(cudaMemcpyAsync(c->host_tail, (char*)c->small.p + kOffStatus, kOffOutLen - kOffStatus + 8,
+                                     cudaMemcpyDeviceToHost, c->stream));
+  if (!rc) rc = from_cuda(cudaStreamSynchronize(c->stream));
+  if (rc) return rc;
+  DevStatus h;
+  std::memcpy(&h, c->host_tail, sizeof(h));
+  std::memcpy(len, (const char*)c->host_tail + (kOffOutLen - kOffStatus), 8);
+  if (h.flags == 0) return LCS_OK;
+  cudaMemset(c->status(), 0, sizeof(DevStatus));
+  return (h.flags & kStatTimeout) ? LCS_ERR_TIMEOUT : LCS_ERR_INTERNAL;
+}
+
 // Latched device status: returns its error (if any) and clears it. Caller has synchronised the stream.
 int take_status(lcs_ctx* c) {
   DevStatus h{};
@@ -120,8 +136,9 @@ static int prep_y(lcs_ctx* c, const uint8_t* d_y, uint64_t n, const Geo& g, bool
   if (!rc && want_rev) rc = from_cuda(ensure(c->peq_r, (size_t)kSigmaMax * g.wpad * 4));
   if (rc) return rc;
   rc = from_cuda(launch_alphabet(d_y, n, c->presence(), c->codemap(), c->sigma(), st));
-  if (!rc) rc = from_cuda(launch_peq(d_y, n, false, g.wpad, c->codemap(), (uint32_t*)c->peq_f.p, st));
-  if (!rc && want_rev) rc = from_cuda(launch_peq(d_y, n, true, g.wpad, c->codemap(), (uint32_t*)c->peq_r.p, st));
+  if (!rc)
+    rc = from_cuda(launch_peq(d_y, n, g.wpad, c->codemap(), c->sigma(), (uint32_t*)c->peq_f.p,
+                              want_rev ? (uint32_t*)c->peq_r.p : nullptr, st));
   return rc;
 }
 
@@ -149,13 +166,13 @@ int run_length(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, u
   if (!rc && split) rc = from_cuda(ensure(c->fv_r, g.wpad * 4));
   if (!rc && split) rc = from_cuda(ensure(c->colsum, (2 * (g.wq + 1) + 4) * 4));
   if (rc) return rc;
-  rc = from_cuda(launch_xoff(d_x, mt, false, 0, Rf, B, c->codemap(), c->sigma(), (uint32_t*)c->xoff_f.p, nullptr, st));
-  if (!rc && split)
-    rc = from_cuda(launch_xoff(d_x + mt, mb, true, padr, Rr, B, c->codemap(), c->sigma(), (uint32_t*)c->xoff_r.p,
-                               nullptr, st));
-  if (!rc) rc = from_cuda(cudaMemsetAsync(c->carry_f.p, 0, g.nblocks * Rf * 4, st));
-  if (!rc && split) rc = from_cuda(cudaMemsetAsync(c->carry_r.p, 0, g.nblocks * Rr * 4, st));
-  if (!rc) rc = from_cuda(cudaMemsetAsync(c->len_acc(), 0, sizeof(unsigned long long), st));
+  {  // row offsets of both tables; the hand-off slots and the length accumulator start at zero
+    const XoffJob xj[2] = {{d_x, mt, 0, 0, Rf, (uint32_t*)c->xoff_f.p, nullptr},
+                           {d_x + mt, mb, 1, padr, Rr, (uint32_t*)c->xoff_r.p, nullptr}};
+    const ZeroSpan zs[3] = {{c->carry_f.p, g.nblocks * Rf * 4}, {c->len_acc(), sizeof(unsigned long long)},
+                            {c->carry_r.p, g.nblocks * Rr * 4}};
+    rc = from_cuda(launch_xoff(xj, split ? 2 : 1, B, c->codemap(), c->sigma(), zs, split ? 3 : 2, st));
+  }
   if (rc) return rc;
   FillJob jobs[2]{};
   jobs[0].xoff = (const uint32_t*)c->xoff_f.p;
@@ -231,14 +248,13 @@ int run_traceback(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y
   if (!rc) rc = from_cuda(ensure(c->sel, S * 4));
   if (!rc) rc = from_cuda(ensure(c->chars, S * (W + 1) * H));
   if (rc) return rc;
-  rc = from_cuda(launch_xoff(d_x, m, false, 0, Rf, B, c->codemap(), c->sigma(), (uint32_t*)c->xoff_f.p,
-                             (uint8_t*)c->xcode.p, st));
-  if (!rc && rev)
-    rc = from_cuda(launch_xoff(d_x, m, true, padr, Rr, B, c->codemap(), c->sigma(), (uint32_t*)c->xoff_r.p, nullptr,
-                               st));
-  if (!rc) rc = from_cuda(cudaMemsetAsync(c->carry_f.p, 0, g.nblocks * Rf * 4, st));
-  if (!rc && rev) rc = from_cuda(cudaMemsetAsync(c->carry_r.p, 0, g.nblocks * Rr * 4, st));
-  if (!rc) rc = from_cuda(cudaMemsetAsync(c->len_acc(), 0, sizeof(unsigned long long), st));
+  {  // row offsets of both tables; hand-off slots, length accumulator and corridor counts start at zero
+    const XoffJob xj[2] = {{d_x, m, 0, 0, Rf, (uint32_t*)c->xoff_f.p, (uint8_t*)c->xcode.p},
+                           {d_x, m, 1, padr, Rr, (uint32_t*)c->xoff_r.p, nullptr}};
+    const ZeroSpan zs[4] = {{c->carry_f.p, g.nblocks * Rf * 4}, {c->len_acc(), sizeof(unsigned long long)},
+                            {c->entcnt.p, S * 4}, {c->carry_r.p, g.nblocks * Rr * 4}};
+    rc = from_cuda(launch_xoff(xj, rev ? 2 : 1, B, c->codemap(), c->sigma(), zs, rev ? 4 : 3, st));
+  }
   if (rc) return rc;
   FillJob jobs[2]{};
   jobs[0].xoff = (const uint32_t*)c->xoff_f.p;
@@ -320,10 +336,11 @@ int run_tables(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, u
   if (!rc) rc = from_cuda(ensure(c->snap_f, g.wpad * 4));
   if (!rc) rc = from_cuda(ensure(c->colsum, tables_sum_words(m, n) * 4));
   if (rc) return rc;
-  rc = from_cuda(launch_xoff(d_x, m, false, 0, Rf, B, c->codemap(), c->sigma(), (uint32_t*)c->xoff_f.p, nullptr,
-                             st));
-  if (!rc) rc = from_cuda(cudaMemsetAsync(c->carry_f.p, 0, g.nblocks * Rf * 4, st));
-  if (!rc) rc = from_cuda(cudaMemsetAsync(c->len_acc(), 0, sizeof(unsigned long long), st));
+  {
+    const XoffJob xj = {d_x, m, 0, 0, Rf, (uint32_t*)c->xoff_f.p, nullptr};
+    const ZeroSpan zs[2] = {{c->carry_f.p, g.nblocks * Rf * 4}, {c->len_acc(), sizeof(unsigned long long)}};
+    rc = from_cuda(launch_xoff(&xj, 1, B, c->codemap(), c->sigma(), zs, 2, st));
+  }
   if (rc) return rc;
   FillJob job{};
   job.xoff = (const uint32_t*)c->xoff_f.p;
@@ -482,10 +499,9 @@ extern "C" int lcs_length(lcs_ctx* c, const uint8_t* x, uint64_t m, const uint8_
   *out_len = 0;
   int rc = stage_inputs(c, x, m, y, n);
   if (!rc) rc = run_length(c, (const uint8_t*)c->x.p, m, (const uint8_t*)c->y.p, n, c->out_len(), c->stream);
-  if (!rc) rc = from_cuda(cudaMemcpyAsync(c->host_word, c->out_len(), 8, cudaMemcpyDeviceToHost, c->stream));
-  if (!rc) rc = from_cuda(cudaStreamSynchronize(c->stream));
-  if (!rc) rc = take_status(c);
-  if (!rc) *out_len = *c->host_word;
+  uint64_t L = 0;
+  if (!rc) rc = fetch_result(c, &L);
+  if (!rc) *out_len = L;
   return rc;
 }
 
@@ -503,15 +519,15 @@ extern "C" int lcs_traceback(lcs_ctx* c, const uint8_t* x, uint64_t m, const uin
   if (!rc)
     rc = run_traceback(c, (const uint8_t*)c->x.p, m, (const uint8_t*)c->y.p, n, (uint8_t*)c->out.p, cap,
                        c->out_len(), c->stream);
-  if (!rc) rc = from_cuda(cudaMemcpyAsync(c->host_word, c->out_len(), 8, cudaMemcpyDeviceToHost, c->stream));
-  if (!rc) rc = from_cuda(cudaStreamSynchronize(c->stream));
-  if (!rc) rc = take_status(c);
+  // the string (at most min(m, n) bytes) comes back with the status and the length, behind one synchronisation
+  const uint64_t take = std::min<uint64_t>(std::min(m, n), out_cap);
+  if (!rc && take) rc = from_cuda(cudaMemcpyAsync(out, c->out.p, take, cudaMemcpyDeviceToHost, c->stream));
+  uint64_t L = 0;
+  if (!rc) rc = fetch_result(c, &L);
   if (rc) return rc;
-  const uint64_t L = *c->host_word;
   *out_len = L;
   if (L > out_cap) return LCS_ERR_CAPACITY;
-  if (L) rc = from_cuda(cudaMemcpy(out, c->out.p, L, cudaMemcpyDeviceToHost));
-  return rc;
+  return LCS_OK;
 }
 
 // Table sizes in bytes; false when they do not fit in 64 bits.

@@ -56,6 +56,7 @@ struct lcs_ctx {
   uint64_t bjobs_at = 0, bitems_at = 0, bsplit_at = 0, border_at = 0;  // byte offsets of the plan's parts in bplan
   cudaStream_t cap_stream = nullptr;
   uint64_t host_word[1] = {0};
+  uint64_t host_tail[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // status word and result length, fetched together
   // stage events of the last profiled call: [0] start, [1] fill start, [2] fill end, [3] end
   bool prof = false, prof_valid = false, prof_trace = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};

@@ -512,9 +512,11 @@ __global__ void __launch_bounds__(kFillThreads, 1) k_fill(const __grid_constant_
 
 template <int B, bool TB, int VG>
 cudaError_t launch_t(const FillArgs& a, cudaStream_t st) {
+  static std::atomic<uint64_t> attr_done{0};  // per template instance: devices whose attribute is set
   auto fn = k_fill<B, TB, VG>;
   const size_t smem = fill_smem_bytes();
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = once_per_device_attr(
+      [&] { return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); }, attr_done);
   if (e != cudaSuccess) return e;
   const unsigned grid = a.job[0].nblocks + (a.njobs > 1 ? a.job[1].nblocks : 0u);
   void* args[] = {const_cast<FillArgs*>(&a)};

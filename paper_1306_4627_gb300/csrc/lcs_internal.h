@@ -1,6 +1,7 @@
 // Internal declarations shared by the CUDA translation units of liblcs.so.
 #pragma once
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -89,15 +90,49 @@ struct TraceArgs {
   DevStatus* status;
 };
 
+// Runs set() (a cudaFuncSetAttribute call) once per device and process; done holds one bit per device.
+template <typename F>
+inline cudaError_t once_per_device_attr(F&& set, std::atomic<uint64_t>& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = dev < 64 ? (1ull << dev) : 0ull;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = set();
+  if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
+
 // ---- launchers (implemented in the .cu files) ------------------------------------------------------------------
 // prep
+constexpr uint64_t kAlphabetOneBlock = 1ull << 18;  // Y up to this length: the alphabet in one block, no clearing
+constexpr int kMaxZeroSpans = 4;
+
+// The row offsets of one table: x (m symbols, read backwards when reverse) after pad_front zero rows, R row-blocks
+// of B rows, kPadRowblocks zero row-blocks in front and kPadBackRowblocks behind; xcode (or nullptr) receives the
+// symbol codes of the m rows.
+struct XoffJob {
+  const uint8_t* x;
+  uint64_t m;
+  int reverse;
+  uint64_t pad_front;
+  uint64_t R;
+  uint32_t* xoff;
+  uint8_t* xcode;
+};
+struct ZeroSpan {  // device words to clear (bytes a multiple of 4)
+  void* p;
+  uint64_t bytes;
+};
+
 cudaError_t launch_alphabet(const uint8_t* y, uint64_t n, uint32_t* presence8, uint16_t* codemap,
                             uint32_t* sigma_rows, cudaStream_t st);
-cudaError_t launch_xoff(const uint8_t* x, uint64_t m, bool reverse, uint64_t pad_front, uint64_t R, uint32_t B,
-                        const uint16_t* codemap, const uint32_t* sigma_rows, uint32_t* xoff, uint8_t* xcode,
-                        cudaStream_t st);
-cudaError_t launch_peq(const uint8_t* y, uint64_t n, bool reverse, uint64_t wpad, const uint16_t* codemap,
-                       uint32_t* peq, cudaStream_t st);
+// the row offsets of up to two jobs and the clearing of up to kMaxZeroSpans spans, in one launch
+cudaError_t launch_xoff(const XoffJob* jobs, int njobs, uint32_t B, const uint16_t* codemap,
+                        const uint32_t* sigma_rows, const ZeroSpan* zero, int nzero, cudaStream_t st);
+// masks of every symbol row 0..sigma for every word < wpad, over Y into peq_f and, if peq_r, over reversed Y
+cudaError_t launch_peq(const uint8_t* y, uint64_t n, uint64_t wpad, const uint16_t* codemap,
+                       const uint32_t* sigma_rows, uint32_t* peq_f, uint32_t* peq_r, cudaStream_t st);
 // fill
 int fill_max_coop_blocks(int device);
 cudaError_t launch_fill(const FillArgs& a, uint32_t B, bool traceback, cudaStream_t st);

@@ -13,6 +13,8 @@
 // entry is the exit of the segment below (or walking the segment itself when the corridor had more columns than
 // walkers). The chosen walkers' symbols are finally copied to the output in order. The result is exactly the walk
 // of Print-LCS; only the order of the work differs.
+#include <atomic>
+
 #include "lcs_internal.h"
 
 namespace lcs {
@@ -266,14 +268,20 @@ __device__ uint64_t walk_segment_warp(const TraceArgs& a, uint64_t hi, uint64_t 
   return j;
 }
 
-// Walker k of segment s (block (s, k / 32), thread k % 32) walks from the k-th corridor column found.
+// Walker k of segment s (block (s, k / 32), thread k % 32) walks from the k-th corridor column found. The last
+// segment has one walker, from (m, n); it records that entry for the chain pass.
 __global__ void k_walk(TraceArgs a) {
   const uint64_t s = blockIdx.x;
   const uint32_t k = blockIdx.y * kWalkers + threadIdx.x;
-  const uint32_t cnt = a.ent_cnt[s];
+  const bool last = s + 1 == a.S;
+  const uint32_t cnt = last ? 1u : a.ent_cnt[s];
   if (k >= (cnt < a.W ? cnt : a.W)) return;
   const uint64_t lo = s * a.H, hi = (s + 1) * a.H < a.m ? (s + 1) * a.H : a.m;
-  const uint64_t e = a.ent[s * a.W + k];
+  const uint64_t e = last ? a.n : a.ent[s * a.W + k];
+  if (last) {
+    a.ent[s * a.W] = (uint32_t)a.n;
+    a.ent_cnt[s] = 1;
+  }
   uint32_t nc = 0;
   const uint64_t x = walk_segment(a, hi, lo, e, a.chars + (s * (a.W + 1) + k) * a.H, &nc);
   a.ext[s * a.W + k] = (uint32_t)x;
@@ -373,12 +381,6 @@ __global__ void k_finalize(TraceArgs a) {
   if (s == 0 && threadIdx.x == 0) *a.out_len = total;
 }
 
-// Segment S-1 starts at (m, n); segments with no boundary corridor data (S == 1) likewise.
-__global__ void k_seed_last(TraceArgs a) {
-  a.ent[(a.S - 1) * a.W] = (uint32_t)a.n;
-  a.ent_cnt[a.S - 1] = 1;
-}
-
 // ---- the full tables c and b of LCS-length (§I.C) from the forward bitmap ----------------------------------------
 // c[i,j] = c[i-1,j] + dv(i,j), where dv(i,j) = c[i,j] - c[i-1,j] is bit j % 32 of T-frame word j / 32 of row i
 // (column 0 reads 0). Rows are cut into chunks of kTabChunk rows: the chunk sums of dv per column, their exclusive
@@ -428,6 +430,8 @@ __global__ void k_tab_expand(TraceArgs a, const uint8_t* y, const uint32_t* sums
   }
 }
 
+std::atomic<uint64_t> chain_attr_done{0};
+
 }  // namespace
 
 cudaError_t launch_combine(const uint32_t* vf, const uint32_t* vr, uint64_t n, uint64_t w, uint32_t* colsum,
@@ -440,10 +444,8 @@ cudaError_t launch_combine(const uint32_t* vf, const uint32_t* vr, uint64_t n, u
   return cudaGetLastError();
 }
 
+// The corridor counts ent_cnt must be zero on entry (the caller clears them with the row offsets).
 cudaError_t launch_traceback(const TraceArgs& a, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(a.ent_cnt, 0, a.S * sizeof(uint32_t), st);
-  if (e != cudaSuccess) return e;
-  k_seed_last<<<1, 1, 0, st>>>(a);
   if (a.S > 1) {
     k_corr_pre<<<(unsigned)(a.S - 1), 1024, 0, st>>>(a);
     uint64_t gx = (a.n + 1 + 255) / 256;
@@ -452,7 +454,12 @@ cudaError_t launch_traceback(const TraceArgs& a, cudaStream_t st) {
   }
   k_walk<<<dim3((unsigned)a.S, a.W / kWalkers), kWalkers, 0, st>>>(a);
   const size_t chain_smem = (size_t)(2 * a.S * kWalkers + a.S) * sizeof(uint32_t);
-  e = cudaFuncSetAttribute(k_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chain_smem);
+  cudaError_t e = once_per_device_attr(
+      [] {
+        return cudaFuncSetAttribute(k_chain, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)((2 * kMaxSegments * kWalkers + kMaxSegments) * sizeof(uint32_t)));
+      },
+      chain_attr_done);
   if (e != cudaSuccess) return e;
   k_chain<<<1, 32, chain_smem, st>>>(a);
   k_finalize<<<(unsigned)a.S, 256, 0, st>>>(a);
