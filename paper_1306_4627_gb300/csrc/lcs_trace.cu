@@ -89,19 +89,35 @@ __global__ void k_corr_pre(TraceArgs a) {
   block_prefix_popc(a.snapR + (a.S - k - 1) * a.wpad, a.w, a.colsum + (2 * (k - 1) + 1) * wp1);
 }
 
+// Thread (q, boundary k): the columns j = 32q .. 32q + 31 (up to n) of the boundary's row. ones_f(j) comes from
+// the forward snapshot's word q, ones_r(n - j) from the at most two words of the reverse snapshot that hold the
+// positions n - 32q - 31 .. n - 32q, so a thread reads six words for its 32 columns.
 __global__ void k_corr_cols(TraceArgs a) {
   const uint64_t k = blockIdx.y + 1;
   const uint64_t wp1 = a.w + 1;
+  const uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t j0 = q * 32;
+  if (j0 > a.n) return;
   const uint32_t* vf = a.snapF + (k - 1) * a.wpad;
   const uint32_t* vr = a.snapR + (a.S - k - 1) * a.wpad;
   const uint32_t* pf = a.colsum + (2 * (k - 1)) * wp1;
   const uint32_t* pr = a.colsum + (2 * (k - 1) + 1) * wp1;
-  const uint64_t target = a.n - *a.L;  // c[i,j] + suffix = n - (ones_f + ones_r); optimal when that sum = n - L
+  const uint32_t target = (uint32_t)(a.n - *a.L);  // c[i,j] + suffix = n - (ones_f + ones_r); optimal at n - L
   const uint64_t s = k - 1;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j <= a.n; j += stride) {
-    const uint32_t sum = ones_prefix(vf, pf, j) + ones_prefix(vr, pr, a.n - j);
-    if (sum == target) {
+  const uint32_t bf = pf[q], wf = vf[q];
+  const uint64_t xb = a.n - j0;                      // the reverse position of column j0 (the largest)
+  const uint64_t qb = xb >> 5;
+  const uint64_t qa = xb >= 31 ? (xb - 31) >> 5 : 0; // the word of the smallest position used
+  const uint32_t bra = pr[qa], wra = vr[qa], brb = pr[qb], wrb = qb < a.w ? vr[qb] : 0u;
+  for (uint32_t t = 0; t < 32; ++t) {
+    const uint64_t j = j0 + t;
+    if (j > a.n) break;
+    const uint64_t x = a.n - j;
+    const uint32_t r = (uint32_t)(x & 31);
+    const bool inb = (x >> 5) == qb;
+    const uint32_t of = bf + (t ? __popc(wf & ((1u << t) - 1u)) : 0u);
+    const uint32_t orr = (inb ? brb : bra) + (r ? __popc((inb ? wrb : wra) & ((1u << r) - 1u)) : 0u);
+    if (of + orr == target) {
       const uint32_t slot = atomicAdd(&a.ent_cnt[s], 1u);
       if (slot < a.W) a.ent[s * a.W + slot] = (uint32_t)j;
     }
@@ -288,24 +304,69 @@ __global__ void k_walk(TraceArgs a) {
   a.nch[s * a.W + k] = nc;
 }
 
-// Follows the true path from (m, n) down the segments (one warp). The first 32 walkers of every segment are staged
-// in shared memory; a segment whose corridor had more columns is searched in global memory, and when its entry
-// is not among its walkers at all (more corridor columns than W) the warp walks the segment itself.
-__global__ void k_chain(TraceArgs a) {
+// Follows the true path from (m, n) down the segments. The first 32 walkers of every segment are staged in shared
+// memory and every block thread links walker k of segment s to the walker of segment s - 1 whose entry is k's exit
+// (if any); thread 0 then follows the links, one shared load per segment. Where a link is missing (the entry is
+// among walkers past the first 32 of a wide corridor, or among none), warp 0 continues segment by segment: it
+// searches all W walkers in global memory, and when the entry is not among them (more corridor columns than W)
+// walks the segment itself.
+constexpr uint32_t kChainThreads = 256;
+constexpr uint8_t kNoLink = 0xFF;
+
+__global__ void __launch_bounds__(kChainThreads) k_chain(TraceArgs a) {
   extern __shared__ uint32_t sm[];
   uint32_t* ent = sm;                         // [S][kWalkers]
   uint32_t* ext = sm + a.S * kWalkers;        // [S][kWalkers]
   uint32_t* cnt = sm + 2 * a.S * kWalkers;    // [S]
-  const uint32_t lane = threadIdx.x;
-  for (uint64_t i = lane; i < a.S * kWalkers; i += 32) {
+  uint8_t* link = reinterpret_cast<uint8_t*>(sm + 2 * a.S * kWalkers + a.S);  // [S][kWalkers]
+  __shared__ int32_t stop_s;
+  __shared__ uint32_t stop_e;
+  const uint32_t tid = threadIdx.x, lane = tid & 31;
+  for (uint64_t i = tid; i < a.S * kWalkers; i += kChainThreads) {
     const uint64_t src = (i / kWalkers) * a.W + (i % kWalkers);
     ent[i] = a.ent[src];
     ext[i] = a.ext[src];
   }
-  for (uint64_t i = lane; i < a.S; i += 32) cnt[i] = a.ent_cnt[i];
-  __syncwarp();
-  uint64_t e = a.n;
-  for (int64_t s = (int64_t)a.S - 1; s >= 0; --s) {
+  for (uint64_t i = tid; i < a.S; i += kChainThreads) cnt[i] = a.ent_cnt[i];
+  __syncthreads();
+  for (uint64_t i = tid; i < a.S * kWalkers; i += kChainThreads) {
+    const uint64_t sg = i / kWalkers, k = i % kWalkers;
+    uint8_t l = kNoLink;
+    const uint32_t c = cnt[sg] < (uint32_t)kWalkers ? cnt[sg] : (uint32_t)kWalkers;
+    if (sg > 0 && k < c) {
+      const uint32_t cb = cnt[sg - 1] < (uint32_t)kWalkers ? cnt[sg - 1] : (uint32_t)kWalkers;
+      const uint32_t x = ext[i];
+      for (uint32_t kk = 0; kk < cb; ++kk)
+        if (ent[(sg - 1) * kWalkers + kk] == x) {
+          l = (uint8_t)kk;
+          break;
+        }
+    }
+    link[i] = l;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    // segment S-1's first walker starts at (m, n)
+    int64_t s = (int64_t)a.S - 1;
+    uint32_t k = 0;
+    stop_s = -1;
+    for (;;) {
+      a.sel[s] = k;
+      if (s == 0) break;
+      const uint8_t nk = link[s * kWalkers + k];
+      if (nk == kNoLink) {
+        stop_s = (int32_t)(s - 1);
+        stop_e = ext[s * kWalkers + k];
+        break;
+      }
+      k = nk;
+      --s;
+    }
+  }
+  __syncthreads();
+  if (tid >= 32 || stop_s < 0) return;
+  uint64_t e = stop_e;
+  for (int64_t s = stop_s; s >= 0; --s) {
     const uint32_t c = cnt[s] < a.W ? cnt[s] : a.W;
     const bool hit = lane < c && ent[s * kWalkers + lane] == (uint32_t)e;
     uint32_t b = __ballot_sync(kFull, hit);
@@ -448,20 +509,20 @@ cudaError_t launch_combine(const uint32_t* vf, const uint32_t* vr, uint64_t n, u
 cudaError_t launch_traceback(const TraceArgs& a, cudaStream_t st) {
   if (a.S > 1) {
     k_corr_pre<<<(unsigned)(a.S - 1), 1024, 0, st>>>(a);
-    uint64_t gx = (a.n + 1 + 255) / 256;
-    if (gx > 1024) gx = 1024;
-    k_corr_cols<<<dim3((unsigned)gx, (unsigned)(a.S - 1)), 256, 0, st>>>(a);
+    const uint64_t gx = (a.n / 32 + 1 + 127) / 128;  // one thread per 32-column word
+    k_corr_cols<<<dim3((unsigned)gx, (unsigned)(a.S - 1)), 128, 0, st>>>(a);
   }
   k_walk<<<dim3((unsigned)a.S, a.W / kWalkers), kWalkers, 0, st>>>(a);
-  const size_t chain_smem = (size_t)(2 * a.S * kWalkers + a.S) * sizeof(uint32_t);
+  const size_t chain_smem = (size_t)(2 * a.S * kWalkers + a.S) * sizeof(uint32_t) + a.S * kWalkers;
   cudaError_t e = once_per_device_attr(
       [] {
-        return cudaFuncSetAttribute(k_chain, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)((2 * kMaxSegments * kWalkers + kMaxSegments) * sizeof(uint32_t)));
+        return cudaFuncSetAttribute(
+            k_chain, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            (int)((2 * kMaxSegments * kWalkers + kMaxSegments) * sizeof(uint32_t) + kMaxSegments * kWalkers));
       },
       chain_attr_done);
   if (e != cudaSuccess) return e;
-  k_chain<<<1, 32, chain_smem, st>>>(a);
+  k_chain<<<1, kChainThreads, chain_smem, st>>>(a);
   k_finalize<<<(unsigned)a.S, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
