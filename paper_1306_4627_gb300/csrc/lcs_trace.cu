@@ -146,23 +146,26 @@ __device__ __forceinline__ uint32_t p_word(const TraceArgs& a, uint32_t code, in
 // the loads of a group overlap; a row whose scan leaves that word reads its words directly.
 __device__ uint64_t walk_segment(const TraceArgs& a, uint64_t hi, uint64_t lo, uint64_t e, uint8_t* out_chars,
                                  uint32_t* out_cnt) {
-  constexpr int kG = 8;
+  constexpr int kG = 16;
   uint64_t i = hi, j = e;
   uint32_t cnt = 0;
+  uint32_t cd[kG];  // symbol codes of the group's rows, requested one group ahead (they do not depend on the walk)
+#pragma unroll
+  for (int k = 0; k < kG; ++k) cd[k] = i > lo + (uint64_t)k ? a.xcode[i - k - 1] : 0u;
   while (i > lo && j > 0) {
     const int64_t Qg = (int64_t)(j >> 5);
-    uint32_t cd[kG], dv[kG], pa[kG], pb[kG];
+    uint32_t dv[kG], pa[kG], pb[kG], ncd[kG];
 #pragma unroll
     for (int k = 0; k < kG; ++k) {
       const bool ok = i > lo + (uint64_t)k;
-      cd[k] = ok ? a.xcode[i - k - 1] : 0u;
       dv[k] = ok ? t_word(a, i - k, (uint64_t)Qg) : 0u;
-    }
-#pragma unroll
-    for (int k = 0; k < kG; ++k) {
-      const bool ok = i > lo + (uint64_t)k;
       pa[k] = ok ? p_word(a, cd[k], Qg) : 0u;
       pb[k] = ok ? p_word(a, cd[k], Qg - 1) : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < kG; ++k) {  // the next group (a group ends early only when the walk ends)
+      const bool ok = i > lo + (uint64_t)(kG + k);
+      ncd[k] = ok ? a.xcode[i - kG - k - 1] : 0u;
     }
 #pragma unroll
     for (int k = 0; k < kG; ++k) {
@@ -200,6 +203,8 @@ __device__ uint64_t walk_segment(const TraceArgs& a, uint64_t hi, uint64_t lo, u
       }
       --i;
     }
+#pragma unroll
+    for (int k = 0; k < kG; ++k) cd[k] = ncd[k];
   }
   *out_cnt = cnt;
   return j;
