@@ -40,11 +40,6 @@ __device__ __forceinline__ void st_relaxed_gpu_if(uint32_t* p, uint32_t v, uint3
       "r"(pred)
       : "memory");
 }
-__device__ __forceinline__ uint32_t lds_u32(uint32_t saddr) {
-  uint32_t v;
-  asm("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(saddr));
-  return v;
-}
 __device__ __forceinline__ uint32_t lds_vol_u32(uint32_t saddr) {
   uint32_t v;
   asm volatile("ld.volatile.shared.u32 %0, [%1];" : "=r"(v) : "r"(saddr) : "memory");

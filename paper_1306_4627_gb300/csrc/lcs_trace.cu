@@ -76,6 +76,53 @@ __global__ void k_combine_min(const uint32_t* vf, const uint32_t* vr, uint64_t n
   if ((threadIdx.x & 31) == 0) atomicMin(colsum + 2 * (w + 1), best);
 }
 
+// Rows up to kCombineOneBlockWords words (n < 65536): prefix popcounts, the minimum and the length in one block.
+constexpr uint64_t kCombineOneBlockWords = 2048;
+
+__global__ void __launch_bounds__(1024) k_combine_small(const uint32_t* vf, const uint32_t* vr, uint64_t n,
+                                                        uint64_t w, unsigned long long* out_len) {
+  __shared__ uint32_t pre[2][kCombineOneBlockWords + 1];
+  __shared__ uint32_t part[1024];
+  __shared__ uint32_t red[32];
+  const uint32_t tid = threadIdx.x;
+  for (int d = 0; d < 2; ++d) {  // pre[d][q] = ones among the first 32 q bits of the row
+    const uint32_t* v = d ? vr : vf;
+    const uint64_t per = (w + 1023) / 1024;
+    const uint64_t q0 = tid * per, q1 = q0 + per < w ? q0 + per : w;
+    uint32_t sum = 0;
+    for (uint64_t q = q0; q < q1; ++q) sum += __popc(v[q]);
+    part[tid] = sum;
+    __syncthreads();
+    for (uint32_t off = 1; off < 1024; off <<= 1) {
+      const uint32_t add = tid >= off ? part[tid - off] : 0u;
+      __syncthreads();
+      part[tid] += add;
+      __syncthreads();
+    }
+    uint32_t run = part[tid] - sum;
+    for (uint64_t q = q0; q < q1; ++q) {
+      pre[d][q] = run;
+      run += __popc(v[q]);
+    }
+    if (tid == 1023) pre[d][w] = part[tid];
+    __syncthreads();
+  }
+  uint32_t best = 0xFFFFFFFFu;
+  for (uint64_t j = tid; j <= n; j += 1024) {
+    const uint64_t x = n - j;
+    const uint32_t of = pre[0][j >> 5] + ((j & 31) ? __popc(vf[j >> 5] & ((1u << (j & 31)) - 1u)) : 0u);
+    const uint32_t orr = pre[1][x >> 5] + ((x & 31) ? __popc(vr[x >> 5] & ((1u << (x & 31)) - 1u)) : 0u);
+    best = of + orr < best ? of + orr : best;
+  }
+  best = __reduce_min_sync(kFull, best);
+  if ((tid & 31) == 0) red[tid >> 5] = best;
+  __syncthreads();
+  if (tid < 32) {
+    best = __reduce_min_sync(kFull, red[tid]);
+    if (tid == 0) *out_len = (unsigned long long)(n - best);
+  }
+}
+
 __global__ void k_combine_fin(const uint32_t* colsum, uint64_t n, uint64_t w, unsigned long long* out_len) {
   *out_len = (unsigned long long)(n - colsum[2 * (w + 1)]);
 }
@@ -502,6 +549,10 @@ std::atomic<uint64_t> chain_attr_done{0};
 
 cudaError_t launch_combine(const uint32_t* vf, const uint32_t* vr, uint64_t n, uint64_t w, uint32_t* colsum,
                            unsigned long long* out_len, cudaStream_t st) {
+  if (w <= kCombineOneBlockWords) {  // one launch: the block keeps both prefix arrays in shared memory
+    k_combine_small<<<1, 1024, 0, st>>>(vf, vr, n, w, out_len);
+    return cudaGetLastError();
+  }
   k_combine_pre<<<2, 1024, 0, st>>>(vf, vr, w, colsum);
   uint64_t blocks = (n + 1 + 255) / 256;
   if (blocks > 2048) blocks = 2048;

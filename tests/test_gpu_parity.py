@@ -148,3 +148,21 @@ def test_full_length_262144_properties(ctx, oracle, sigma):
 def test_full_length_262144_oracle(ctx, oracle, sigma):
     x, y = gen.pair_uniform(262144, 262144, sigma, seed=gen.BASE_SEED + 2)
     assert ctx.length(x, y) == oracle.lcs_length(x, y)
+
+
+@pytest.mark.parametrize("n", [(1 << 18), (1 << 18) + 1])
+def test_alphabet_paths_around_one_block_limit(ctx, oracle, n):
+    """Y up to 2^18 symbols: the alphabet in one block; longer: the multi-block presence. Both give the oracle's
+    length and string; all 256 byte values present exercises the largest alphabet."""
+    x, y = gen.pair_uniform(600, n, 256, seed=4100 + n % 7)
+    assert ctx.length(x, y) == oracle.lcs_length(x, y)
+    assert ctx.traceback(x, y) == oracle.lcs_traceback(x, y)
+
+
+def test_reused_context_after_alphabet_change(ctx, oracle):
+    """Consecutive calls on one context with different alphabets: no state of one call leaks into the next (the
+    masks are rewritten in full, the scratch words cleared in the row-offset launch)."""
+    for k, sigma in enumerate([256, 4, 20, 4, 256]):
+        x, y = gen.pair_uniform(1500 + 17 * k, 3000 - 31 * k, sigma, seed=4200 + k)
+        assert ctx.length(x, y) == oracle.lcs_length(x, y)
+        assert ctx.traceback(x, y) == oracle.lcs_traceback(x, y)
