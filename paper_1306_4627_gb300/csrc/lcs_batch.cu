@@ -6,8 +6,8 @@
 //   * the add inside a lane ripples through its 4 words with the carry flag;
 //   * the lanes of a group run skewed by one row each (lane g works on row t - g at step t), so the carry out of a
 //     lane's 128 bits for a row is shuffled to the next lane, which adds it in the same row one step later;
-//   * a warp works on 32 / G pairs of the same group size at once, G chosen per pair as the smallest power of two
-//     with 4 * G words >= ceil(n / 32) (so short pairs share a warp and long pairs spread over it).
+//   * a warp works on floor(32 / G) pairs of the same group size at once, G = ceil(ceil(n / 32) / 4) lanes per
+//     pair (so short pairs share a warp and long pairs spread over it).
 // The host plans the launch: it buckets pairs by G, orders work items (up to 32 / G pairs each) by decreasing
 // rows, and a persistent kernel lets every warp take the next item from an atomic ticket. A pair with many rows is
 // split in two jobs that run at the same time, its top half forward and its bottom half on the reversed strings;
@@ -386,18 +386,17 @@ __global__ void __launch_bounds__(kBatchWarps * 32) k_batch_main(BatchArgs a) {
 #pragma unroll
       for (int b = 0; b < 8; ++b) cq[b] = nq[b];
     }
-    // c[m, n] = zero bits of V over the pair's n columns (bits past n stay 1), summed over the group's lanes
-    // (every lane of the warp takes part in the shuffles, whatever its group holds)
-    uint32_t z = 0;
-#pragma unroll
-    for (int k = 0; k < kBK; ++k) z += __popc(~V[k]);
-    for (uint32_t off = 1; off < G; off <<= 1) z += __shfl_xor_sync(kFull, z, off);
     if (has && pr.mt < pr.m) {
       // a split pair: keep the job's final row for the combine kernel
       uint4* dst = reinterpret_cast<uint4*>(a.fvbuf + (uint64_t)(pr.fv + job.rev) * kWarpWords + gl * kBK);
       *dst = make_uint4(V[0], V[1], V[2], V[3]);
-    } else if (has && gl == 0) {
-      a.out_lens[pr.out] = z;
+    } else if (has) {
+      // c[m, n] = zero bits of V over the pair's n columns (bits past n stay 1): every lane of the group adds its
+      // share to the length, which starts at zero
+      uint32_t z = 0;
+#pragma unroll
+      for (int k = 0; k < kBK; ++k) z += __popc(~V[k]);
+      if (z) atomicAdd(reinterpret_cast<unsigned long long*>(a.out_lens + pr.out), (unsigned long long)z);
     }
   }
 }
@@ -450,11 +449,8 @@ __global__ void __launch_bounds__(256) k_batch_combine(BatchArgs a) {
   }
 }
 
-inline uint32_t group_lanes(uint32_t w) {
-  uint32_t g = 1;
-  while (g < 32 && g * kBK < w) g <<= 1;
-  return g;
-}
+// Lanes per pair: just enough to hold its words, 4 per lane (so 32 / G pairs share a warp).
+inline uint32_t group_lanes(uint32_t w) { return w == 0 ? 1u : (w + kBK - 1) / kBK; }
 
 struct Plan {
   std::vector<BPair> pairs;
