@@ -316,11 +316,22 @@ def alu_peak_tops(sm_mhz: float, sms: int = 152) -> float:
 
 def run_batch_workload(args):
     """10000 independent pairs (m, n log-uniform in [64, 4096]; alphabet 4 for half, 20 for the other half),
-    lengths only, one persistent launch per step; plus the same pairs as sequential single-pair launches."""
+    lengths only, one persistent launch per step; plus the same pairs as sequential single-pair launches. Under
+    torchrun the batch is split over the ranks by pair (cells balanced, no data exchanged) and value = all cells /
+    the slowest rank's time."""
     import torch
-    from paper_1306_4627_gb300 import gen, lcs
-    dev = torch.device("cuda", 0)
-    pairs = gen.batch_pairs()
+    from paper_1306_4627_gb300 import gen, lcs, shard
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    all_pairs = gen.batch_pairs()
+    total_cells = int(sum(len(x) * len(y) for x, y in all_pairs))
+    parts = shard.partition_pairs([len(x) for x, _ in all_pairs], [len(y) for _, y in all_pairs], ws)
+    pairs = [all_pairs[k] for k in parts[rank]]
     xs = np.concatenate([x for x, _ in pairs])
     ys = np.concatenate([y for _, y in pairs])
     xo = np.zeros(len(pairs) + 1, np.int64)
@@ -331,12 +342,14 @@ def run_batch_workload(args):
     dxs, dys = torch.from_numpy(xs).to(dev), torch.from_numpy(ys).to(dev)
     dxo, dyo = torch.from_numpy(xo).to(dev), torch.from_numpy(yo).to(dev)
     out = torch.zeros(len(pairs), dtype=torch.int64, device=dev)
-    ctx = lcs.Context(0)
+    ctx = lcs.Context(local)
     stream = torch.cuda.Stream(device=dev)
     for _ in range(args.warmup):
         ctx.batch_dev(dxs, dxo, dys, dyo, len(pairs), out, stream=stream)
     ctx.sync()
-    sampler = ClockSampler(0)
+    sampler = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
     sampler.start()
     time.sleep(0.3)
     # per call (the plan is reused and the launches replay as a CUDA graph): CUDA events on the call's stream
@@ -384,32 +397,37 @@ def run_batch_workload(args):
     ctx.sync()
     seq_s = time.perf_counter() - t0
     seq_cells = sum(len(pairs[i][0]) * len(pairs[i][1]) for i in sample)
-    t_ms = float(np.median(tot)) * 1e3
-    k_ms = float(np.median(kern))
+    t_ms = max_over_ranks(float(np.median(tot)) * 1e3, dist, dev)
+    k_ms = max_over_ranks(float(np.median(kern)), dist, dev)
+    e2e_s = max_over_ranks(float(np.median(e2e)), dist, dev)
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     peak = alu_peak_tops(sm_mhz)
-    achieved = cells / 32 * 4 / (k_ms * 1e-3) / 1e12
+    achieved = total_cells / ws / 32 * 4 / (k_ms * 1e-3) / 1e12  # per GPU (the shards are cell-balanced)
     line = {
-        "metric": METRIC, "value": cells / (t_ms * 1e-3) / 1e9, "unit": "GCUPS", "n_gpus": 1,
+        "metric": METRIC, "value": total_cells / (t_ms * 1e-3) / 1e9, "unit": "GCUPS", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "scaling": "strong", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": "batch: 10000 pairs, m and n log-uniform in [64, 4096], sigma 4 (half) and 20 (half), "
-                               "lengths only", "cells": cells, "pairs": len(pairs)},
+                               "lengths only", "cells": total_cells, "pairs": len(all_pairs),
+                   "parallelism": f"pairs split over {ws} ranks, cells balanced" if ws > 1 else "1 GPU"},
         "stages_ms": {"prep": float(np.median(prep)), "batch_kernel": k_ms},
-        "kernel_gcups": cells / (k_ms * 1e-3) / 1e9,
+        "kernel_gcups": total_cells / (k_ms * 1e-3) / 1e9,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
                      "traffic": None, "kernel": "k_batch_main",
                      "note": "algorithmic work = 4 INT32 ops per 32 cells; peak = 152 SMs x 64 INT32/clk x sampled "
                              "SM clock"},
         "sequential_per_pair": {"gcups": seq_cells / seq_s / 1e9, "pairs_timed": len(sample),
-                                "speedup_of_batch": (cells / (t_ms * 1e-3)) / (seq_cells / seq_s),
+                                "speedup_of_batch": (total_cells / ws / (t_ms * 1e-3)) / (seq_cells / seq_s),
                                 "note": "lcs_length_dev per pair, back to back, same GPU"},
-        "e2e": {"value": cells / float(np.median(e2e)) / 1e9, "unit": "GCUPS",
+        "e2e": {"value": total_cells / e2e_s / 1e9, "unit": "GCUPS",
                 "h2d_bytes_per_step": int(xs.nbytes + ys.nbytes), "d2h_bytes_per_step": 8 * len(pairs)},
         "gpu_launches": 3 * args.steps, "clocks": clocks,  # k_batch_prep, k_batch_main, k_batch_combine per call
     }
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
 
 
 def run_long_workload(args):
