@@ -146,9 +146,5 @@ cudaError_t launch_traceback(const TraceArgs& t, cudaStream_t st);
 cudaError_t launch_tables(const TraceArgs& t, const uint8_t* y, uint32_t* sums, uint32_t* c, uint8_t* b,
                           cudaStream_t st);
 uint64_t tables_sum_words(uint64_t m, uint64_t n);
-// batch
-struct BatchPlan;
-// misc
-cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
 
 }  // namespace lcs

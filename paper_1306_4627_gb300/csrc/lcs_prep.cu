@@ -241,6 +241,4 @@ cudaError_t launch_peq(const uint8_t* y, uint64_t n, uint64_t wpad, const uint16
   return cudaGetLastError();
 }
 
-cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st) { return cudaMemsetAsync(p, 0, bytes, st); }
-
 }  // namespace lcs
