@@ -17,6 +17,7 @@
 #include <cstring>
 #include <mutex>
 #include <numeric>
+#include <new>
 #include <vector>
 
 #include "lcs_ctx.h"
@@ -571,35 +572,46 @@ static int batch_blocks_per_sm(lcs_ctx* c, int occ) {
   return want < occ ? want : occ;
 }
 
-// The launches of a planned batch: zero the outputs, per-pair prep, the persistent kernel (stage events around
-// them when profiling).
-static void batch_launches(lcs_ctx* c, uint64_t* d_out, uint64_t count, const BatchArgs& a, cudaStream_t st,
-                           bool marks) {
+// Device facts the batch launches need, looked up once per context.
+static cudaError_t batch_geometry(lcs_ctx* c) {
+  if (c->b_sms > 0) return cudaSuccess;
+  int sms = 0, prep_per_sm = 0, main_per_sm = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&prep_per_sm, k_batch_prep, 256, 0);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&main_per_sm, k_batch_main, kBatchWarps * 32, 0);
+  if (e != cudaSuccess) return e;
+  c->b_sms = std::max(sms, 1);
+  c->b_prep_per_sm = std::max(prep_per_sm, 1);
+  c->b_main_occ = std::max(main_per_sm, 1);
+  return cudaSuccess;
+}
+
+// The launches of a planned batch: zero the outputs, per-pair prep, the persistent kernel, the join of split pairs
+// (stage events around them when profiling). Returns the first error.
+static cudaError_t batch_launches(lcs_ctx* c, uint64_t* d_out, uint64_t count, const BatchArgs& a, cudaStream_t st,
+                                  bool marks) {
   if (marks) c->mark(0, st);
-  cudaMemsetAsync(d_out, 0, count * sizeof(uint64_t), st);  // empty pairs: length 0
-  if (a.npairs) {
-    cudaMemsetAsync(a.ticket, 0, 8, st);
-    cudaMemsetAsync(a.xcode, 0, kCodeZeros * sizeof(uint16_t), st);
-    int sms = 0, per_sm = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-    int prep_per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&prep_per_sm, k_batch_prep, 256, 0);
-    const unsigned prep_blocks =
-        (unsigned)std::min<uint64_t>((a.npairs + 7) / 8, (uint64_t)sms * std::max(prep_per_sm, 1));
+  cudaError_t e = cudaMemsetAsync(d_out, 0, count * sizeof(uint64_t), st);  // empty pairs: length 0
+  if (e == cudaSuccess && a.npairs) {
+    e = cudaMemsetAsync(a.ticket, 0, 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.xcode, 0, kCodeZeros * sizeof(uint16_t), st);
+    if (e != cudaSuccess) return e;
+    const uint64_t sms = (uint64_t)c->b_sms;
+    const unsigned prep_blocks = (unsigned)std::min<uint64_t>((a.npairs + 7) / 8, sms * c->b_prep_per_sm);
     k_batch_prep<<<prep_blocks, 256, 0, st>>>(a);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_main, kBatchWarps * 32, 0);
-    per_sm = batch_blocks_per_sm(c, per_sm);
-    const unsigned blocks = (unsigned)std::max(1, sms * std::max(per_sm, 1));
+    const unsigned blocks = (unsigned)(sms * batch_blocks_per_sm(c, c->b_main_occ));
     if (marks) c->mark(1, st);
     k_batch_main<<<blocks, kBatchWarps * 32, 0, st>>>(a);
-    if (a.nsplit)
-      k_batch_combine<<<(unsigned)std::min<uint64_t>((a.nsplit + 7) / 8, (uint64_t)sms * 8), 256, 0, st>>>(a);
+    if (a.nsplit) k_batch_combine<<<(unsigned)std::min<uint64_t>((a.nsplit + 7) / 8, sms * 8), 256, 0, st>>>(a);
     if (marks) c->mark(2, st);
     c->bblocks = blocks;
+    e = cudaGetLastError();
   } else if (marks) {
     c->mark(1, st);
     c->mark(2, st);
   }
+  return e;
 }
 
 // Runs a batch whose xs / ys / out_lens are already on the device. The first call of a batch plans it on the host,
@@ -620,10 +632,9 @@ int run_batch(lcs_ctx* c, const uint8_t* d_xs, const uint8_t* d_ys, const uint64
     c->bvalid = false;
     Plan plan;
     c->bbig.clear();
-    int sms = 0, per_sm = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_main, kBatchWarps * 32, 0);
-    make_plan(x_off, y_off, count, (uint64_t)std::max(sms, 1) * std::max(per_sm, 1) * kBatchWarps, plan, c->bbig);
+    rc = from_cuda(batch_geometry(c));
+    if (rc) return rc;
+    make_plan(x_off, y_off, count, (uint64_t)c->b_sms * c->b_main_occ * kBatchWarps, plan, c->bbig);
     c->bcells = 0;
     for (uint64_t k = 0; k < count; ++k) c->bcells += (x_off[k + 1] - x_off[k]) * (y_off[k + 1] - y_off[k]);
     const size_t pb = plan.pairs.size() * sizeof(BPair), jb = plan.jobs.size() * sizeof(BJob),
@@ -681,8 +692,7 @@ int run_batch(lcs_ctx* c, const uint8_t* d_xs, const uint8_t* d_ys, const uint64
   a.nitems = (uint32_t)c->bnitems;
   a.nsplit = (uint32_t)c->bnsplit;
   if (c->prof || fresh) {
-    batch_launches(c, d_out, count, a, st, c->prof);
-    rc = from_cuda(cudaGetLastError());
+    rc = from_cuda(batch_launches(c, d_out, count, a, st, c->prof));
   } else {
     if (!c->bexec) {
       if (!c->cap_stream) {
@@ -692,9 +702,10 @@ int run_batch(lcs_ctx* c, const uint8_t* d_xs, const uint8_t* d_ys, const uint64
       // capture: the recorded launches do not run now; the graph runs on st below
       rc = from_cuda(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
       if (rc) return rc;
-      batch_launches(c, d_out, count, a, c->cap_stream, false);
+      const cudaError_t le = batch_launches(c, d_out, count, a, c->cap_stream, false);
       cudaGraph_t graph = nullptr;
       rc = from_cuda(cudaStreamEndCapture(c->cap_stream, &graph));
+      if (!rc && le != cudaSuccess) rc = from_cuda(le);
       if (!rc) rc = from_cuda(cudaGraphInstantiate(&c->bexec, graph, 0));
       if (graph) cudaGraphDestroy(graph);
       if (rc) {
@@ -729,7 +740,7 @@ static bool offsets_ok(const uint64_t* off, uint64_t count) {
   return true;
 }
 
-extern "C" int lcs_batch_dev(lcs_ctx* c, const uint8_t* d_xs, const uint64_t* d_x_off, const uint8_t* d_ys,
+static int lcs_batch_dev_impl(lcs_ctx* c, const uint8_t* d_xs, const uint64_t* d_x_off, const uint8_t* d_ys,
                              const uint64_t* d_y_off, uint64_t count, uint64_t* d_out_lens, void* stream) {
   if (!c || (count && (!d_x_off || !d_y_off || !d_out_lens))) return LCS_ERR_INVALID;
   if (count == 0) return LCS_OK;
@@ -746,7 +757,18 @@ extern "C" int lcs_batch_dev(lcs_ctx* c, const uint8_t* d_xs, const uint64_t* d_
   return run_batch(c, d_xs + xo[0], d_ys + yo[0], xo.data(), yo.data(), count, d_out_lens, st);
 }
 
-extern "C" int lcs_batch(lcs_ctx* c, const uint8_t* xs, const uint64_t* x_off, const uint8_t* ys,
+extern "C" int lcs_batch_dev(lcs_ctx* c, const uint8_t* d_xs, const uint64_t* d_x_off, const uint8_t* d_ys,
+                             const uint64_t* d_y_off, uint64_t count, uint64_t* d_out_lens, void* stream) {
+  try {  // no C++ exception crosses the C boundary
+    return lcs_batch_dev_impl(c, d_xs, d_x_off, d_ys, d_y_off, count, d_out_lens, stream);
+  } catch (const std::bad_alloc&) {
+    return LCS_ERR_NOMEM;
+  } catch (...) {
+    return LCS_ERR_INTERNAL;
+  }
+}
+
+static int lcs_batch_impl(lcs_ctx* c, const uint8_t* xs, const uint64_t* x_off, const uint8_t* ys,
                          const uint64_t* y_off, uint64_t count, uint64_t* out_lens) {
   if (!c || (count && (!x_off || !y_off || !out_lens))) return LCS_ERR_INVALID;
   if (count == 0) return LCS_OK;
@@ -767,4 +789,15 @@ extern "C" int lcs_batch(lcs_ctx* c, const uint8_t* xs, const uint64_t* x_off, c
   if (!rc) rc = from_cuda(cudaStreamSynchronize(c->stream));
   if (!rc) rc = take_status(c);
   return rc;
+}
+
+extern "C" int lcs_batch(lcs_ctx* c, const uint8_t* xs, const uint64_t* x_off, const uint8_t* ys,
+                         const uint64_t* y_off, uint64_t count, uint64_t* out_lens) {
+  try {  // no C++ exception crosses the C boundary
+    return lcs_batch_impl(c, xs, x_off, ys, y_off, count, out_lens);
+  } catch (const std::bad_alloc&) {
+    return LCS_ERR_NOMEM;
+  } catch (...) {
+    return LCS_ERR_INTERNAL;
+  }
 }

@@ -39,6 +39,7 @@ struct lcs_ctx {
   uint32_t fill_B_tb = 8;     // rows per systolic step of traceback fills
   uint32_t fill_variant = 0;     // length-only fills: bits 1-2 select the hand-off validation group (see launch_fill)
   uint32_t fill_variant_tb = 0;  // the same for traceback fills
+  int b_sms = 0, b_prep_per_sm = 0, b_main_occ = 0;  // batch: SMs and blocks per SM (looked up once)
   int batch_blocks_per_sm = 0;  // persistent batch kernel blocks per SM (0 = one)
   uint32_t debug_drop = 0;    // test hook (environment LCS_DEBUG_DROP_HANDOFF): a hand-off that never comes
   std::mutex mu;

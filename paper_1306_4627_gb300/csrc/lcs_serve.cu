@@ -15,6 +15,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -86,30 +87,41 @@ struct lcs_server {
     std::vector<Req*> take;
     std::vector<uint8_t> xs, ys;
     std::vector<uint64_t> xo, yo, out;
+    try {
+      take.reserve(cfg.max_batch);  // filled under the lock below without allocating
+    } catch (...) {
+    }
     for (;;) {
       {
         std::unique_lock<std::mutex> lk(mu);
         cv_work.wait(lk, [&] { return stop || !q_short.empty(); });
         if (q_short.empty() && stop) return;
         take.clear();
-        while (!q_short.empty() && take.size() < cfg.max_batch) {
+        const size_t cap = std::min<size_t>(cfg.max_batch, std::max<size_t>(take.capacity(), 1));
+        while (!q_short.empty() && take.size() < cap) {
           take.push_back(q_short.front());
           q_short.pop_front();
         }
       }
-      xs.clear();
-      ys.clear();
-      xo.assign(1, 0);
-      yo.assign(1, 0);
-      for (Req* r : take) {
-        xs.insert(xs.end(), r->x.begin(), r->x.end());
-        ys.insert(ys.end(), r->y.begin(), r->y.end());
-        xo.push_back(xs.size());
-        yo.push_back(ys.size());
+      int rc = LCS_OK;
+      try {
+        xs.clear();
+        ys.clear();
+        xo.assign(1, 0);
+        yo.assign(1, 0);
+        for (Req* r : take) {
+          xs.insert(xs.end(), r->x.begin(), r->x.end());
+          ys.insert(ys.end(), r->y.begin(), r->y.end());
+          xo.push_back(xs.size());
+          yo.push_back(ys.size());
+        }
+        out.assign(take.size(), 0);
+      } catch (...) {
+        rc = LCS_ERR_NOMEM;
       }
-      out.assign(take.size(), 0);
-      const int rc = lcs_batch(c, xs.empty() ? nullptr : xs.data(), xo.data(), ys.empty() ? nullptr : ys.data(),
-                               yo.data(), take.size(), out.data());
+      if (!rc)
+        rc = lcs_batch(c, xs.empty() ? nullptr : xs.data(), xo.data(), ys.empty() ? nullptr : ys.data(), yo.data(),
+                       take.size(), out.data());
       for (size_t k = 0; k < take.size(); ++k) {
         take[k]->status = rc;
         take[k]->length = rc == LCS_OK ? out[k] : 0;
@@ -143,11 +155,15 @@ struct lcs_server {
       const uint8_t* x = r->x.empty() ? nullptr : r->x.data();
       const uint8_t* y = r->y.empty() ? nullptr : r->y.data();
       if (r->flags & LCS_TRACEBACK) {
-        r->lcs.resize(std::max<size_t>(1, std::min(r->x.size(), r->y.size())));
         uint64_t len = 0;
-        r->status = lcs_traceback(c, x, r->x.size(), y, r->y.size(), r->lcs.data(), r->lcs.size(), &len);
+        try {
+          r->lcs.resize(std::max<size_t>(1, std::min(r->x.size(), r->y.size())));
+          r->status = lcs_traceback(c, x, r->x.size(), y, r->y.size(), r->lcs.data(), r->lcs.size(), &len);
+        } catch (...) {
+          r->status = LCS_ERR_NOMEM;
+        }
         r->length = len;
-        r->lcs.resize(r->status == LCS_OK ? len : 0);
+        r->lcs.resize(r->status == LCS_OK ? len : 0);  // shrinking: no allocation
         // give large bitmaps back, so that the budget is what the device actually holds
         if (c->T.cap > (256ull << 20)) {
           cudaSetDevice(c->device);
@@ -164,7 +180,7 @@ struct lcs_server {
   }
 };
 
-extern "C" int lcs_serve_create(lcs_ctx* ctx, const lcs_serve_cfg* cfg, lcs_server** out) {
+static int lcs_serve_create_impl(lcs_ctx* ctx, const lcs_serve_cfg* cfg, lcs_server** out) {
   if (!ctx || !out) return LCS_ERR_INVALID;
   *out = nullptr;
   lcs_server* s = new (std::nothrow) lcs_server();
@@ -188,52 +204,93 @@ extern "C" int lcs_serve_create(lcs_ctx* ctx, const lcs_serve_cfg* cfg, lcs_serv
     }
     s->budget = (uint64_t)(free_b * 0.6);
   }
-  for (uint32_t k = 0; k < 1 + s->cfg.pair_workers; ++k) {
-    lcs_ctx* c = nullptr;
-    const int rc = lcs_ctx_create(s->device, &c);
-    if (rc) {
-      for (lcs_ctx* d : s->ctxs) lcs_ctx_destroy(d);
-      delete s;
-      return rc;
+  int rc = LCS_OK;
+  try {
+    s->ctxs.reserve(1 + s->cfg.pair_workers);
+    s->threads.reserve(1 + s->cfg.pair_workers);
+    for (uint32_t k = 0; k < 1 + s->cfg.pair_workers && !rc; ++k) {
+      lcs_ctx* c = nullptr;
+      rc = lcs_ctx_create(s->device, &c);
+      if (!rc) s->ctxs.push_back(c);
     }
-    s->ctxs.push_back(c);
+    if (!rc) {
+      s->threads.emplace_back(&lcs_server::batch_worker, s, s->ctxs[0]);
+      for (uint32_t k = 0; k < s->cfg.pair_workers; ++k)
+        s->threads.emplace_back(&lcs_server::pair_worker, s, s->ctxs[1 + k]);
+    }
+  } catch (...) {  // a thread that could not start: stop the ones that did
+    rc = LCS_ERR_INTERNAL;
   }
-  s->threads.emplace_back(&lcs_server::batch_worker, s, s->ctxs[0]);
-  for (uint32_t k = 0; k < s->cfg.pair_workers; ++k)
-    s->threads.emplace_back(&lcs_server::pair_worker, s, s->ctxs[1 + k]);
+  if (rc) {
+    {
+      std::lock_guard<std::mutex> g(s->mu);
+      s->stop = true;
+    }
+    s->cv_work.notify_all();
+    for (auto& t : s->threads) t.join();
+    for (lcs_ctx* d : s->ctxs) lcs_ctx_destroy(d);
+    delete s;
+    return rc;
+  }
   *out = s;
   return LCS_OK;
 }
 
-extern "C" int lcs_serve_submit(lcs_server* s, const uint8_t* x, uint64_t m, const uint8_t* y, uint64_t n,
+extern "C" int lcs_serve_create(lcs_ctx* ctx, const lcs_serve_cfg* cfg, lcs_server** out) {
+  try {  // no C++ exception crosses the C boundary
+    return lcs_serve_create_impl(ctx, cfg, out);
+  } catch (const std::bad_alloc&) {
+    return LCS_ERR_NOMEM;
+  } catch (...) {
+    return LCS_ERR_INTERNAL;
+  }
+}
+
+static int lcs_serve_submit_impl(lcs_server* s, const uint8_t* x, uint64_t m, const uint8_t* y, uint64_t n,
                                 uint32_t flags, uint64_t* ticket) {
   if (!s || !ticket || (m && !x) || (n && !y) || (flags & ~LCS_TRACEBACK)) return LCS_ERR_INVALID;
   if (m >= (1ull << 32) || n >= (1ull << 32)) return LCS_ERR_INVALID;
   const bool tb = (flags & LCS_TRACEBACK) != 0;
   const uint64_t need = tb && m && n ? traceback_bytes(m, n) : 0;
   if (need > s->budget) return LCS_ERR_NOMEM;
-  Req* r = new (std::nothrow) Req();
-  if (!r) return LCS_ERR_NOMEM;
-  r->x.assign(x, x + m);
-  r->y.assign(y, y + n);
+  std::unique_ptr<Req> owned(new (std::nothrow) Req());
+  if (!owned) return LCS_ERR_NOMEM;
+  owned->x.assign(x, x + m);  // may throw bad_alloc: the request is freed by owned
+  owned->y.assign(y, y + n);
+  Req* r = owned.get();
   r->flags = flags;
   r->bitmap = need;
   r->short_pair = !tb && n <= 4096 && m * n < s->long_cells;
   r->t_submit = now_s();
   {
     std::lock_guard<std::mutex> g(s->mu);
-    if (s->stop || s->live >= s->cfg.max_queue) {
-      delete r;
-      return s->stop ? LCS_ERR_INVALID : LCS_ERR_BUSY;
-    }
+    if (s->stop || s->live >= s->cfg.max_queue) return s->stop ? LCS_ERR_INVALID : LCS_ERR_BUSY;
     r->ticket = s->next_ticket++;
+    auto& q = r->short_pair ? s->q_short : s->q_pair;
     s->reqs[r->ticket] = r;
+    try {
+      q.push_back(r);
+    } catch (...) {
+      s->reqs.erase(r->ticket);
+      throw;
+    }
     ++s->live;
-    (r->short_pair ? s->q_short : s->q_pair).push_back(r);
+    owned.release();  // the server owns the request now
   }
   s->cv_work.notify_all();
   *ticket = r->ticket;
   return LCS_OK;
+}
+
+extern "C" int lcs_serve_submit(lcs_server* s, const uint8_t* x, uint64_t m, const uint8_t* y, uint64_t n,
+                                uint32_t flags, uint64_t* ticket) {
+  try {  // no C++ exception crosses the C boundary
+    return lcs_serve_submit_impl(s, x, m, y, n, flags, ticket);
+  } catch (const std::bad_alloc&) {
+    return LCS_ERR_NOMEM;
+  } catch (...) {
+    return LCS_ERR_INTERNAL;
+  }
 }
 
 static void fill_result(const Req* r, lcs_result* out) {
