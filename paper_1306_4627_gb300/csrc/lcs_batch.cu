@@ -298,6 +298,54 @@ __device__ __forceinline__ void add4c(const uint32_t (&v)[kBK], const uint32_t (
         "r"(take));
 }
 
+// The rows of one item for one lane. STAGED: the masks come from the warp's shared stage (lane_stage points at this
+// lane's 4 words of row 0; row r is kWarpWords words further), else from the pair's table in L2. The masks of the
+// next step are loaded one step ahead, the symbol codes eight steps ahead.
+template <bool STAGED>
+__device__ __forceinline__ void run_rows(uint32_t (&V)[kBK], const uint32_t* lane_stage, const uint32_t* peq,
+                                         uint64_t tab, uint32_t w, uint32_t w0, bool has, const uint16_t* xp,
+                                         uint32_t jend, uint32_t gl, uint32_t take, uint32_t steps) {
+  auto load_p = [&](uint32_t code, uint32_t (&P)[kBK]) {
+    if (STAGED) {
+      const uint4 q = *reinterpret_cast<const uint4*>(lane_stage + code * kWarpWords);
+      P[0] = q.x; P[1] = q.y; P[2] = q.z; P[3] = q.w;
+    } else {
+#pragma unroll
+      for (int k = 0; k < kBK; ++k) {
+        const uint32_t q = w0 + k;
+        P[k] = (has && q < w) ? __ldg(peq + tab + (uint64_t)code * w + q) : 0u;
+      }
+    }
+  };
+  auto codes8 = [&](uint32_t t0, uint32_t (&c)[8]) {
+    const uint32_t r0 = min(t0 + kCodePadFront - gl, jend);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) c[b] = __ldg(xp + r0 + b);
+  };
+  uint32_t cin = 0;
+  uint32_t cq[8], nq[8], P[kBK], Pn[kBK];
+  codes8(0, cq);
+  load_p(cq[0], Pn);
+  for (uint32_t t0 = 0; t0 < steps; t0 += 8) {
+    codes8(t0 + 8, nq);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+#pragma unroll
+      for (int k = 0; k < kBK; ++k) P[k] = Pn[k];
+      load_p(b + 1 < 8 ? cq[b + 1 < 8 ? b + 1 : 0] : nq[0], Pn);  // the next step's masks, one step ahead
+      uint32_t U[kBK], S[kBK], cout;
+#pragma unroll
+      for (int k = 0; k < kBK; ++k) U[k] = V[k] & P[k];
+      add4c(V, U, cin, take, S, cout);
+      cin = __shfl_up_sync(kFull, cout, 1);
+#pragma unroll
+      for (int k = 0; k < kBK; ++k) V[k] = S[k] | (V[k] & ~P[k]);
+    }
+#pragma unroll
+    for (int b = 0; b < 8; ++b) cq[b] = nq[b];
+  }
+}
+
 __global__ void __launch_bounds__(kBatchWarps * 32) k_batch_main(BatchArgs a) {
   __shared__ __align__(16) uint32_t stage_s[kBatchWarps][kStageRows * kWarpWords];
   const uint32_t wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -338,18 +386,6 @@ __global__ void __launch_bounds__(kBatchWarps * 32) k_batch_main(BatchArgs a) {
       }
       __syncwarp();
     }
-    auto load_p = [&](uint32_t code, uint32_t (&P)[kBK]) {
-      if (staged) {
-        const uint4 q = *reinterpret_cast<const uint4*>(&stage[code * kWarpWords + lane * kBK]);
-        P[0] = q.x; P[1] = q.y; P[2] = q.z; P[3] = q.w;
-      } else {
-#pragma unroll
-        for (int k = 0; k < kBK; ++k) {
-          const uint32_t q = w0 + k;
-          P[k] = (has && q < pr.w) ? __ldg(a.peq + tab + (uint64_t)code * pr.w + q) : 0u;
-        }
-      }
-    };
     // Lane gl of a group works on row t - gl at step t (a skew of one row per lane), so the carry out of its 128
     // bits for that row reaches lane gl + 1 by one shuffle, in time for the same row at step t + 1. Rows before 0
     // or past the job read the zero-row codes around the job's list: a row without a match leaves V unchanged.
@@ -357,36 +393,13 @@ __global__ void __launch_bounds__(kBatchWarps * 32) k_batch_main(BatchArgs a) {
     // whose staged row is zero for them).
     const uint16_t* xp = has ? a.xcode + (job.rev ? pr.xcr : pr.xcf) - kCodePadFront : a.xcode;
     const uint32_t jend = has ? job.rows + kCodePadFront : 0u;  // rows from here on read the padding only
-    auto codes8 = [&](uint32_t t0, uint32_t (&c)[8]) {
-      const uint32_t r0 = min(t0 + kCodePadFront - gl, jend);
-#pragma unroll
-      for (int b = 0; b < 8; ++b) c[b] = __ldg(xp + r0 + b);
-    };
-    uint32_t V[kBK] = {kFull, kFull, kFull, kFull};
-    uint32_t cin = 0;
     const uint32_t take = gl ? kFull : 0u;  // the first lane of a group starts every row without a carry
     const uint32_t steps = (item.rows + G - 1 + 7) & ~7u;
-    uint32_t cq[8], nq[8], P[kBK], Pn[kBK];
-    codes8(0, cq);
-    load_p(cq[0], Pn);
-    for (uint32_t t0 = 0; t0 < steps; t0 += 8) {
-      codes8(t0 + 8, nq);
-#pragma unroll
-      for (int b = 0; b < 8; ++b) {
-#pragma unroll
-        for (int k = 0; k < kBK; ++k) P[k] = Pn[k];
-        load_p(b + 1 < 8 ? cq[b + 1 < 8 ? b + 1 : 0] : nq[0], Pn);  // the next step's masks, one step ahead
-        uint32_t U[kBK], S[kBK], cout;
-#pragma unroll
-        for (int k = 0; k < kBK; ++k) U[k] = V[k] & P[k];
-        add4c(V, U, cin, take, S, cout);
-        cin = __shfl_up_sync(kFull, cout, 1);
-#pragma unroll
-        for (int k = 0; k < kBK; ++k) V[k] = S[k] | (V[k] & ~P[k]);
-      }
-#pragma unroll
-      for (int b = 0; b < 8; ++b) cq[b] = nq[b];
-    }
+    uint32_t V[kBK] = {kFull, kFull, kFull, kFull};
+    if (staged)
+      run_rows<true>(V, stage + lane * kBK, a.peq, tab, pr.w, w0, has, xp, jend, gl, take, steps);
+    else
+      run_rows<false>(V, stage + lane * kBK, a.peq, tab, pr.w, w0, has, xp, jend, gl, take, steps);
     if (has && pr.mt < pr.m) {
       // a split pair: keep the job's final row for the combine kernel
       uint4* dst = reinterpret_cast<uint4*>(a.fvbuf + (uint64_t)(pr.fv + job.rev) * kWarpWords + gl * kBK);
