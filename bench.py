@@ -12,7 +12,12 @@ between timed steps outside the events). `e2e` times the same step through the h
 (host->device copy of X and Y, device->host copy of the result, inside the timed region). `--impl reference` times
 the CPU oracle instead, on the host cores, on a bounded sample of the same workload (the first rows of X).
 Under torchrun (N > 1) every rank runs its own replica of the step on its own GPU (the single-pair path does not
-shard); value = total cells of all ranks / the slowest rank's time.
+shard); value = total cells of all ranks / the slowest rank's time. Before timing, the library's autotuner picks the
+fill configuration on the pair (--no-autotune keeps the default).
+
+Other workloads (--workload): batch (10000 pairs in one persistent launch; split over ranks by pair under
+torchrun), long (262144^2, length only), serve (Poisson request streams through the server), table1 (the shapes of
+the paper's Table 1 against the serial and the multi-threaded CPU oracle).
 """
 
 from __future__ import annotations

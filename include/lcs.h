@@ -54,9 +54,8 @@ LCS_API const char* lcs_strerror(int status);
 /* ---- context ------------------------------------------------------------------------------------------------ */
 typedef struct lcs_ctx lcs_ctx;
 
-/* Creates a context on CUDA device `device`: its own non-blocking streams, grow-only device scratch buffers and
- * pinned staging buffers. *out receives the handle. Errors: LCS_ERR_INVALID (out NULL or no such device),
- * LCS_ERR_CUDA. */
+/* Creates a context on CUDA device `device`: its own non-blocking stream and grow-only device scratch buffers.
+ * *out receives the handle. Errors: LCS_ERR_INVALID (out NULL or no such device), LCS_ERR_CUDA. */
 LCS_API int lcs_ctx_create(int device, lcs_ctx** out);
 
 /* Waits for all work of the context and frees everything it owns. NULL is ignored. */
