@@ -63,7 +63,7 @@ void release(DBuf& b) {
 // Copies the status word and the result length of the call just enqueued on the context's stream back in one
 // transfer, waits for the stream, and returns the latched error (clearing it) or LCS_OK with *len.
 int fetch_result(lcs_ctx* c, uint64_t* len) {
-  static_assert(kOffOutLen > kOffStatus && kOffOutLen - kOffStatus + 8 <= sizeof(c->host_tail), "layout");
+  static_assert(kOffOutLen > kOffStatus && kOffOutLen - kOffStatus + 8 <= 8 * sizeof(uint64_t), "layout");
   int rc = from_cuda(cudaMemcpyAsync(c->host_tail, (char*)c->small.p + kOffStatus, kOffOutLen - kOffStatus + 8,
                                      cudaMemcpyDeviceToHost, c->stream));
   if (!rc) rc = from_cuda(cudaStreamSynchronize(c->stream));
@@ -384,6 +384,7 @@ extern "C" int lcs_ctx_create(int device, lcs_ctx** out) {
   int rc = from_cuda(cudaSetDevice(device));
   if (!rc) rc = from_cuda(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
   if (!rc) rc = from_cuda(ensure(c->small, kSmallBytes));
+  if (!rc) rc = from_cuda(cudaMallocHost((void**)&c->host_tail, 8 * sizeof(uint64_t)));
   if (!rc) rc = from_cuda(cudaMemset(c->small.p, 0, kSmallBytes));
   if (!rc) {
     c->max_coop = fill_max_coop_blocks(device);
@@ -411,6 +412,7 @@ extern "C" void lcs_ctx_destroy(lcs_ctx* c) {
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   if (c->stream) cudaStreamDestroy(c->stream);
+  if (c->host_tail) cudaFreeHost(c->host_tail);
   delete c;
 }
 
@@ -482,11 +484,42 @@ extern "C" int lcs_traceback_dev(lcs_ctx* c, const uint8_t* d_x, uint64_t m, con
 }
 
 // Copies host inputs into the context's device buffers.
+// Grows the pinned host staging area to at least `bytes` (the old contents are not kept). The caller has waited for
+// every copy that used it.
+static int ensure_hstage(lcs_ctx* c, size_t bytes) {
+  if (bytes <= c->hstage_cap) return LCS_OK;
+  if (c->hstage) cudaFreeHost(c->hstage);
+  c->hstage = nullptr;
+  c->hstage_cap = 0;
+  const size_t want = std::max<size_t>(bytes + bytes / 4, 4096);
+  void* p = nullptr;
+  const int rc = from_cuda(cudaMallocHost(&p, want));
+  if (rc) return rc;
+  c->hstage = static_cast<uint8_t*>(p);
+  c->hstage_cap = want;
+  return LCS_OK;
+}
+
+// Pairs up to this many input bytes go through the pinned staging area (a host copy, then asynchronous copies);
+// larger inputs are copied from the caller's memory directly.
+constexpr uint64_t kStageBytesMax = 64ull << 20;
+
+// Copies host inputs into the context's device buffers (through pinned staging for inputs up to kStageBytesMax).
+// The previous call on the context has finished (its result was fetched), so the staging area is free.
 static int stage_inputs(lcs_ctx* c, const uint8_t* x, uint64_t m, const uint8_t* y, uint64_t n) {
   int rc = from_cuda(ensure(c->x, std::max<uint64_t>(m, 1)));
   if (!rc) rc = from_cuda(ensure(c->y, std::max<uint64_t>(n, 1)));
-  if (!rc && m) rc = from_cuda(cudaMemcpyAsync(c->x.p, x, m, cudaMemcpyHostToDevice, c->stream));
-  if (!rc && n) rc = from_cuda(cudaMemcpyAsync(c->y.p, y, n, cudaMemcpyHostToDevice, c->stream));
+  if (rc) return rc;
+  const uint8_t* sx = x;
+  const uint8_t* sy = y;
+  if (m + n <= kStageBytesMax && ensure_hstage(c, m + n) == LCS_OK) {
+    if (m) std::memcpy(c->hstage, x, m);
+    if (n) std::memcpy(c->hstage + m, y, n);
+    sx = c->hstage;
+    sy = c->hstage + m;
+  }
+  if (m) rc = from_cuda(cudaMemcpyAsync(c->x.p, sx, m, cudaMemcpyHostToDevice, c->stream));
+  if (!rc && n) rc = from_cuda(cudaMemcpyAsync(c->y.p, sy, n, cudaMemcpyHostToDevice, c->stream));
   return rc;
 }
 
@@ -519,14 +552,18 @@ extern "C" int lcs_traceback(lcs_ctx* c, const uint8_t* x, uint64_t m, const uin
   if (!rc)
     rc = run_traceback(c, (const uint8_t*)c->x.p, m, (const uint8_t*)c->y.p, n, (uint8_t*)c->out.p, cap,
                        c->out_len(), c->stream);
-  // the string (at most min(m, n) bytes) comes back with the status and the length, behind one synchronisation
+  // the string (at most min(m, n) bytes) comes back with the status and the length, behind one synchronisation;
+  // through the pinned staging area when it holds it (the input copies from it are done by then: stream order)
   const uint64_t take = std::min<uint64_t>(std::min(m, n), out_cap);
-  if (!rc && take) rc = from_cuda(cudaMemcpyAsync(out, c->out.p, take, cudaMemcpyDeviceToHost, c->stream));
+  const bool staged = take && c->hstage && take <= c->hstage_cap;
+  if (!rc && take)
+    rc = from_cuda(cudaMemcpyAsync(staged ? c->hstage : out, c->out.p, take, cudaMemcpyDeviceToHost, c->stream));
   uint64_t L = 0;
   if (!rc) rc = fetch_result(c, &L);
   if (rc) return rc;
   *out_len = L;
   if (L > out_cap) return LCS_ERR_CAPACITY;
+  if (staged && L) std::memcpy(out, c->hstage, L);
   return LCS_OK;
 }
 

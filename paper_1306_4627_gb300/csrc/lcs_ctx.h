@@ -56,8 +56,11 @@ struct lcs_ctx {
   uint64_t bcells = 0, bblocks = 0, bnpairs = 0, bnitems = 0, bnsplit = 0;
   uint64_t bjobs_at = 0, bitems_at = 0, bsplit_at = 0, border_at = 0;  // byte offsets of the plan's parts in bplan
   cudaStream_t cap_stream = nullptr;
-  uint64_t host_word[1] = {0};
-  uint64_t host_tail[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // status word and result length, fetched together
+  // pinned host memory: the status word and result length of a call (fetched together), and a staging area for
+  // host-buffer calls' inputs and traceback output (copies from pinned memory run asynchronously)
+  uint64_t* host_tail = nullptr;  // 8 words
+  uint8_t* hstage = nullptr;
+  size_t hstage_cap = 0;
   // stage events of the last profiled call: [0] start, [1] fill start, [2] fill end, [3] end
   bool prof = false, prof_valid = false, prof_trace = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -74,6 +77,9 @@ struct lcs_ctx {
   uint64_t* out_len() { return (uint64_t*)((char*)small.p + lcs::kOffOutLen); }
 
   void release_all() {
+    if (hstage) cudaFreeHost(hstage);
+    hstage = nullptr;
+    hstage_cap = 0;
     if (bexec) cudaGraphExecDestroy(bexec);
     bexec = nullptr;
     bvalid = false;
