@@ -486,7 +486,7 @@ extern "C" int lcs_traceback_dev(lcs_ctx* c, const uint8_t* d_x, uint64_t m, con
 // Copies host inputs into the context's device buffers.
 // Grows the pinned host staging area to at least `bytes` (the old contents are not kept). The caller has waited for
 // every copy that used it.
-static int ensure_hstage(lcs_ctx* c, size_t bytes) {
+int ensure_hstage(lcs_ctx* c, size_t bytes) {
   if (bytes <= c->hstage_cap) return LCS_OK;
   if (c->hstage) cudaFreeHost(c->hstage);
   c->hstage = nullptr;
@@ -500,19 +500,26 @@ static int ensure_hstage(lcs_ctx* c, size_t bytes) {
   return LCS_OK;
 }
 
-// Pairs up to this many input bytes go through the pinned staging area (a host copy, then asynchronous copies);
-// larger inputs are copied from the caller's memory directly.
-constexpr uint64_t kStageBytesMax = 64ull << 20;
+// True when p is page-locked host memory (copies from it run asynchronously without the driver's staging).
+bool host_pinned(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeHost;
+}
 
-// Copies host inputs into the context's device buffers (through pinned staging for inputs up to kStageBytesMax).
-// The previous call on the context has finished (its result was fetched), so the staging area is free.
+// Copies host inputs into the context's device buffers. Pageable inputs up to kStageBytesMax go through the pinned
+// staging area (a host copy, then asynchronous copies); pinned inputs and larger ones are copied directly. The
+// previous call on the context has finished (its result was fetched), so the staging area is free.
 static int stage_inputs(lcs_ctx* c, const uint8_t* x, uint64_t m, const uint8_t* y, uint64_t n) {
   int rc = from_cuda(ensure(c->x, std::max<uint64_t>(m, 1)));
   if (!rc) rc = from_cuda(ensure(c->y, std::max<uint64_t>(n, 1)));
   if (rc) return rc;
   const uint8_t* sx = x;
   const uint8_t* sy = y;
-  if (m + n <= kStageBytesMax && ensure_hstage(c, m + n) == LCS_OK) {
+  if (m + n <= kStageBytesMax && !(m && host_pinned(x)) && ensure_hstage(c, m + n) == LCS_OK) {
     if (m) std::memcpy(c->hstage, x, m);
     if (n) std::memcpy(c->hstage + m, y, n);
     sx = c->hstage;

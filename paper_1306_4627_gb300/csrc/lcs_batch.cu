@@ -25,6 +25,8 @@
 namespace lcs {
 int take_status(lcs_ctx* c);
 }  // namespace lcs
+int ensure_hstage(lcs_ctx* c, size_t bytes);  // lcs_api.cu: pinned staging area of a context
+bool host_pinned(const void* p);
 
 namespace {
 
@@ -793,14 +795,29 @@ static int lcs_batch_impl(lcs_ctx* c, const uint8_t* xs, const uint64_t* x_off, 
   int rc = from_cuda(ensure(c->x, std::max<uint64_t>(nx, 1)));
   if (!rc) rc = from_cuda(ensure(c->y, std::max<uint64_t>(ny, 1)));
   if (!rc) rc = from_cuda(ensure(c->bout, count * 8));
-  if (!rc && nx) rc = from_cuda(cudaMemcpyAsync(c->x.p, xs + x_off[0], nx, cudaMemcpyHostToDevice, c->stream));
-  if (!rc && ny) rc = from_cuda(cudaMemcpyAsync(c->y.p, ys + y_off[0], ny, cudaMemcpyHostToDevice, c->stream));
+  if (rc) return rc;
+  // small pageable batches go through the context's pinned staging area (host copies, then asynchronous copies)
+  const uint8_t* sx = xs + x_off[0];
+  const uint8_t* sy = ys + y_off[0];
+  const bool stage = nx + ny + count * 8 <= kStageBytesMax && !(nx && host_pinned(sx)) &&
+                     ensure_hstage(c, nx + ny + count * 8) == LCS_OK;
+  if (stage) {
+    if (nx) std::memcpy(c->hstage, sx, nx);
+    if (ny) std::memcpy(c->hstage + nx, sy, ny);
+    sx = c->hstage;
+    sy = c->hstage + nx;
+  }
+  if (nx) rc = from_cuda(cudaMemcpyAsync(c->x.p, sx, nx, cudaMemcpyHostToDevice, c->stream));
+  if (!rc && ny) rc = from_cuda(cudaMemcpyAsync(c->y.p, sy, ny, cudaMemcpyHostToDevice, c->stream));
   if (!rc)
     rc = run_batch(c, (const uint8_t*)c->x.p, (const uint8_t*)c->y.p, x_off, y_off, count, (uint64_t*)c->bout.p,
                    c->stream);
-  if (!rc) rc = from_cuda(cudaMemcpyAsync(out_lens, c->bout.p, count * 8, cudaMemcpyDeviceToHost, c->stream));
+  uint64_t* land = stage ? reinterpret_cast<uint64_t*>(c->hstage + ((nx + ny + 7) & ~(uint64_t)7)) : out_lens;
+  if (stage && (uint8_t*)(land + count) > c->hstage + c->hstage_cap) land = out_lens;
+  if (!rc) rc = from_cuda(cudaMemcpyAsync(land, c->bout.p, count * 8, cudaMemcpyDeviceToHost, c->stream));
   if (!rc) rc = from_cuda(cudaStreamSynchronize(c->stream));
   if (!rc) rc = take_status(c);
+  if (!rc && land != out_lens) std::memcpy(out_lens, land, count * 8);
   return rc;
 }
 

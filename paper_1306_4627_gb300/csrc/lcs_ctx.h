@@ -27,6 +27,7 @@ constexpr size_t kOffStatus = 576;     // DevStatus (16 B)
 constexpr size_t kOffOutLen = 608;     // uint64_t
 constexpr size_t kOffTicket = 640;     // uint32_t[2] work tickets of the persistent batch kernels
 constexpr size_t kSmallBytes = 1024;
+constexpr uint64_t kStageBytesMax = 4ull << 20;  // pageable host inputs up to this size go through pinned staging
 
 }  // namespace lcs
 
