@@ -188,9 +188,9 @@ __device__ __forceinline__ uint32_t p_word(const TraceArgs& a, uint32_t code, in
 }
 
 // Walks rows hi..lo+1 from column e; returns the exit column (at row lo); writes emitted symbols to out_chars.
-// The rows are taken 8 at a time: the symbol codes, bitmap words and match-mask words of the next 8 rows at the
-// walk's current 32-column word are requested together (the walk usually stays in one word for many rows), so
-// the loads of a group overlap; a row whose scan leaves that word reads its words directly.
+// The rows are taken 16 at a time: the bitmap and match-mask words of the group's rows at the walk's current
+// 32-column word are requested together (the walk usually stays in one word for many rows), with the symbol codes
+// of the next group, so the loads of a group overlap; a row whose scan leaves that word reads its words directly.
 __device__ uint64_t walk_segment(const TraceArgs& a, uint64_t hi, uint64_t lo, uint64_t e, uint8_t* out_chars,
                                  uint32_t* out_cnt) {
   constexpr int kG = 16;
@@ -374,7 +374,8 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(TraceArgs a) {
   __shared__ int32_t stop_s;
   __shared__ uint32_t stop_e;
   const uint32_t tid = threadIdx.x, lane = tid & 31;
-  for (uint64_t i = tid; i < a.S * kWalkers; i += kChainThreads) {
+#pragma unroll 8
+  for (uint64_t i = tid; i < a.S * kWalkers; i += kChainThreads) {  // the loads of 8 rounds in flight together
     const uint64_t src = (i / kWalkers) * a.W + (i % kWalkers);
     ent[i] = a.ent[src];
     ext[i] = a.ext[src];
