@@ -11,8 +11,9 @@
  * differs.
  *
  * Storage: b at one byte per cell (processors write disjoint bytes), c as rolling rows inside each block plus
- * the last column of every block for all rows (read by the block to its right). Meant for the paper's problem
- * sizes (Table 1: up to 10000 x 1500) and test cases, not for m*n in the billions.
+ * the last column of every block for all rows (read by the block to its right). The traceback is meant for the
+ * paper's problem sizes (Table 1: up to 10000 x 1500) and test cases; oracle_lcs_length_par keeps no b and runs at
+ * any size whose edge columns fit (threads * m words).
  */
 #include <pthread.h>
 #include <sched.h>
@@ -30,7 +31,7 @@ typedef struct {
   int nproc;
   uint64_t* j0;               /* block p covers columns j0[p] .. j0[p+1]-1 (1-based) */
   uint32_t* edge;             /* edge[p * (m + 1) + i] = c[i, j0[p+1] - 1] */
-  uint8_t* b;                 /* b[(i - 1) * n + (j - 1)] */
+  uint8_t* b;                 /* b[(i - 1) * n + (j - 1)], or NULL for the length only */
   volatile uint64_t* done;    /* done[p] = rows of block p finished (published with release order) */
 } ParShared;
 
@@ -66,18 +67,31 @@ static void* par_fill_block(void* arg) {
       cur[0] = left ? left[i] : 0;   /* c[i, ja-1] */
       prev[0] = left ? left[i - 1] : 0; /* c[i-1, ja-1] */
       const uint8_t xi = s->x[i - 1];
-      for (uint64_t k = 1; k <= w; ++k) {
-        const uint64_t j = ja - 1 + k;
-        uint8_t* bc = &s->b[(i - 1) * s->n + (j - 1)];
-        if (xi == s->y[j - 1]) {
-          cur[k] = prev[k - 1] + 1;
-          *bc = PAR_DIAG;
-        } else if (prev[k] >= cur[k - 1]) {
-          cur[k] = prev[k];
-          *bc = PAR_UP;
-        } else {
-          cur[k] = cur[k - 1];
-          *bc = PAR_LEFT;
+      if (s->b) {
+        for (uint64_t k = 1; k <= w; ++k) {
+          const uint64_t j = ja - 1 + k;
+          uint8_t* bc = &s->b[(i - 1) * s->n + (j - 1)];
+          if (xi == s->y[j - 1]) {
+            cur[k] = prev[k - 1] + 1;
+            *bc = PAR_DIAG;
+          } else if (prev[k] >= cur[k - 1]) {
+            cur[k] = prev[k];
+            *bc = PAR_UP;
+          } else {
+            cur[k] = cur[k - 1];
+            *bc = PAR_LEFT;
+          }
+        }
+      } else {  /* the same recurrence without the arrows */
+        for (uint64_t k = 1; k <= w; ++k) {
+          const uint64_t j = ja - 1 + k;
+          if (xi == s->y[j - 1]) {
+            cur[k] = prev[k - 1] + 1;
+          } else if (prev[k] >= cur[k - 1]) {
+            cur[k] = prev[k];
+          } else {
+            cur[k] = cur[k - 1];
+          }
         }
       }
       mine[i] = cur[w];
@@ -174,4 +188,54 @@ int oracle_lcs_traceback_par(const uint8_t* x, uint64_t m, const uint8_t* y, uin
   free(tid);
   free(rev);
   return rc;
+}
+
+/* LCS-length (§I.C), length only, filled by `threads` processors in column blocks as above; c[m, n], or UINT64_MAX
+ * when memory runs out. The row arrays and the blocks' edge columns take O(threads * m + n) words, so this runs
+ * at sizes where the table b could not be stored. */
+uint64_t oracle_lcs_length_par(const uint8_t* x, uint64_t m, const uint8_t* y, uint64_t n, int threads) {
+  if (m == 0 || n == 0) return 0;
+  if (threads < 1) threads = 1;
+  int np = threads;
+  if ((uint64_t)np > n) np = (int)n;
+  ParShared s;
+  memset(&s, 0, sizeof(s));
+  s.x = x;
+  s.y = y;
+  s.m = m;
+  s.n = n;
+  s.nproc = np;
+  s.rows_per_chunk = m < 256 ? m : 256;
+  s.b = NULL;
+  s.j0 = (uint64_t*)malloc((size_t)(np + 1) * sizeof(uint64_t));
+  s.edge = (uint32_t*)calloc((size_t)np * (m + 1), sizeof(uint32_t));
+  s.done = (volatile uint64_t*)calloc((size_t)np, sizeof(uint64_t));
+  ParTask* tasks = (ParTask*)calloc((size_t)np, sizeof(ParTask));
+  pthread_t* tid = (pthread_t*)calloc((size_t)np, sizeof(pthread_t));
+  uint64_t len = UINT64_MAX;
+  if (s.j0 && s.edge && s.done && tasks && tid) {
+    for (int p = 0; p <= np; ++p) s.j0[p] = 1 + (n * (uint64_t)p) / (uint64_t)np;
+    int started = 0;
+    for (int p = 0; p < np; ++p) {
+      tasks[p].s = &s;
+      tasks[p].p = p;
+      tasks[p].rc = PAR_OK;
+      if (p == 0) continue;
+      if (pthread_create(&tid[p], NULL, par_fill_block, &tasks[p]) != 0) break;
+      started = p;
+    }
+    par_fill_block(&tasks[0]);
+    for (int p = started + 1; p < np; ++p) par_fill_block(&tasks[p]); /* blocks whose thread did not start */
+    for (int p = 1; p <= started; ++p) pthread_join(tid[p], NULL);
+    int ok = 1;
+    for (int p = 0; p < np; ++p)
+      if (tasks[p].rc != PAR_OK) ok = 0;
+    if (ok) len = s.edge[(uint64_t)(np - 1) * (m + 1) + m];
+  }
+  free(s.j0);
+  free(s.edge);
+  free((void*)s.done);
+  free(tasks);
+  free(tid);
+  return len;
 }

@@ -5,8 +5,9 @@ no code with the CUDA library and never calls it.
 
 * `lcs_length`, `lcs_traceback`, `lcs_tables`: ctypes calls into `lcs_oracle.c`, the literal LCS-length (§I.C)
   and Print-LCS (§I.D) of Dash & Nayak with the paper's tie-break (UP when c[i-1,j] >= c[i,j-1]).
-* `lcs_traceback_par`: `lcs_oracle_par.c`, the same fill split into column blocks over host threads (the
-  paper's parallel algorithm, §II.A-B); a CPU baseline for the paper's own experiment (Table 1).
+* `lcs_traceback_par`, `lcs_length_par`: `lcs_oracle_par.c`, the same fill split into column blocks over host
+  threads (the paper's parallel algorithm, §II.A-B); a CPU baseline for the paper's own experiment (Table 1), and
+  the length at sizes the serial loop takes minutes for.
 * `brute_force`: the exhaustive method the paper contrasts with dynamic programming (§I and §I.A): enumerate all
   2^m subsequences of X, keep those that are also subsequences of Y, and return the largest length together with
   the set of all common subsequences of that length. Exponential; only for m <= 16.
@@ -59,6 +60,8 @@ def _load():
             lib.oracle_lcs_tables.restype = ctypes.c_int
             lib.oracle_lcs_traceback_par.argtypes = [u8p, u64, u8p, u64, u8p, u64, ctypes.POINTER(u64), ctypes.c_int]
             lib.oracle_lcs_traceback_par.restype = ctypes.c_int
+            lib.oracle_lcs_length_par.argtypes = [u8p, u64, u8p, u64, ctypes.c_int]
+            lib.oracle_lcs_length_par.restype = u64
             _lib = lib
     return _lib
 
@@ -120,6 +123,15 @@ def lcs_traceback_par(x, y, threads: int) -> bytes:
     if rc != 0:
         raise RuntimeError(f"oracle_lcs_traceback_par failed: {rc}")
     return out[: n_out.value].tobytes()
+
+
+def lcs_length_par(x, y, threads: int) -> int:
+    """c[m, n] with the fill split into column blocks over `threads` host threads (§II.A-B), length only."""
+    x, y = _u8(x), _u8(y)
+    v = _load().oracle_lcs_length_par(_ptr(x), len(x), _ptr(y), len(y), int(threads))
+    if v == 2**64 - 1:
+        raise MemoryError("oracle: out of memory")
+    return int(v)
 
 
 def is_subsequence(z: bytes, s: bytes) -> bool:

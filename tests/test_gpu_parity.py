@@ -143,11 +143,16 @@ def test_full_length_262144_properties(ctx, oracle, sigma):
 
 
 @pytest.mark.slow
-@pytest.mark.skipif(os.environ.get("LCS_FULL_ORACLE") != "1", reason="full 262144^2 oracle run takes minutes")
 @pytest.mark.parametrize("sigma", [4, 20])
 def test_full_length_262144_oracle(ctx, oracle, sigma):
+    """The full 262144^2 length against the oracle's recurrence, filled in column blocks on all host cores (the
+    serial oracle takes minutes per pair; LCS_SERIAL_ORACLE=1 uses it)."""
     x, y = gen.pair_uniform(262144, 262144, sigma, seed=gen.BASE_SEED + 2)
-    assert ctx.length(x, y) == oracle.lcs_length(x, y)
+    if os.environ.get("LCS_SERIAL_ORACLE") == "1":
+        want = oracle.lcs_length(x, y)
+    else:
+        want = oracle.lcs_length_par(x, y, os.cpu_count() or 1)
+    assert ctx.length(x, y) == want
 
 
 @pytest.mark.parametrize("n", [(1 << 18), (1 << 18) + 1])

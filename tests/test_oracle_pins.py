@@ -215,3 +215,17 @@ def test_parallel_oracle_edges(oracle):
     assert oracle.lcs_traceback_par(x, x, 4) == x
     for x, y, L, s in read_golden_cases(GOLDEN)[0]:
         assert oracle.lcs_traceback_par(x, y, 3) == s
+
+
+@pytest.mark.parametrize("threads", [1, 2, 7])
+def test_parallel_length_oracle_equals_serial(oracle, threads):
+    rng = np.random.default_rng(90 + threads)
+    for k in range(20):
+        m = int(rng.integers(1, 700))
+        n = int(rng.integers(1, 400))
+        alpha = [b"AB", b"ACGT", bytes(range(20))][k % 3]
+        x = bytes(rng.choice(list(alpha), m).astype(np.uint8))
+        y = bytes(rng.choice(list(alpha), n).astype(np.uint8))
+        assert oracle.lcs_length_par(x, y, threads) == oracle.lcs_length(x, y), (m, n)
+    assert oracle.lcs_length_par(b"", b"ACGT", 3) == 0
+    assert oracle.lcs_length_par(b"ACGT" * 100, b"ACGT" * 100, 64) == 400  # more threads than needed
