@@ -176,6 +176,40 @@ LCS_API int lcs_batch(lcs_ctx* ctx, const uint8_t* xs, const uint64_t* x_off, co
 LCS_API int lcs_batch_dev(lcs_ctx* ctx, const uint8_t* d_xs, const uint64_t* d_x_off, const uint8_t* d_ys,
                   const uint64_t* d_y_off, uint64_t count, uint64_t* d_out_lens, void* stream);
 
+/* Batch configuration (no counterpart in the paper: how the batched fill of §I.C is laid out on the GPU). The rows
+ * of a pair are worked by a group of lanes of one warp, each lane holding consecutive 32-column words of the row.
+ *   words_per_lane: 2, 4 or 8 words per lane (a pair whose row does not fit 32 lanes at that width uses the next
+ *                   larger; pairs with more than 4096 columns go through the single-pair path). Default 4.
+ *   split_pct:      job height. A pair whose rows exceed split_pct % of the average rows per resident warp (and at
+ *                   least 256) runs as two half-height jobs, the bottom half on the reversed strings, joined at the
+ *                   middle row. 0 = never split. Default 100.
+ *   blocks_per_sm:  resident blocks (8 warps each) of the persistent kernel per SM, 1 or 2; capped by shared memory
+ *                   (a batch with 8 words per lane runs one). Default 1.
+ *   reserved:       0.
+ * Every configuration gives the same lengths; only the time differs. A new configuration takes effect at the next
+ * lcs_batch* call (the cached plan of the last batch is dropped). */
+typedef struct lcs_batch_config {
+  uint32_t words_per_lane;
+  uint32_t split_pct;
+  uint32_t blocks_per_sm;
+  uint32_t reserved;
+} lcs_batch_config;
+
+LCS_API int lcs_ctx_get_batch_config(lcs_ctx* ctx, lcs_batch_config* out);
+/* LCS_ERR_INVALID when a field is out of range (words_per_lane not 2/4/8, split_pct > 1000, blocks_per_sm not 1/2,
+ * reserved not 0). */
+LCS_API int lcs_ctx_set_batch_config(lcs_ctx* ctx, const lcs_batch_config* cfg);
+
+/* Batch autotuner: runs the batch given as for lcs_batch_dev (device buffers and offsets, d_out_lens receives the
+ * lengths) under every configuration (words per lane 2/4/8 x split_pct 50/100/200/never x blocks per SM 1/2): a
+ * planning call and a graph-capturing call, then three timed replays each (events on `stream`); keeps the
+ * configuration with the fastest median in the context and returns it
+ * in *best with its median time in *best_ms (either may be NULL). Blocking. Every configuration's lengths are
+ * compared with the first one's; a difference returns LCS_ERR_INTERNAL and keeps the previous configuration. */
+LCS_API int lcs_ctx_autotune_batch_dev(lcs_ctx* ctx, const uint8_t* d_xs, const uint64_t* d_x_off, const uint8_t* d_ys,
+                                       const uint64_t* d_y_off, uint64_t count, uint64_t* d_out_lens, void* stream,
+                                       lcs_batch_config* best, double* best_ms);
+
 /* ---- serving: continuous batching of requests that arrive over time ------------------------------------------- */
 typedef struct lcs_server lcs_server;
 

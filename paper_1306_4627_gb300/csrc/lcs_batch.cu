@@ -2,17 +2,18 @@
 //
 // Every pair is a small instance of the same bit-parallel row update as the single-pair fill (U = V & P;
 // S = V + U; V' = S | (V & ~P), one 32-column word per register). Here the rows of a pair are processed by a group
-// of G lanes of a warp, each lane holding K = 4 consecutive words of the row:
-//   * the add inside a lane ripples through its 4 words with the carry flag;
+// of G lanes of a warp, each lane holding K consecutive words of the row (K = 2, 4 or 8 words per lane):
+//   * the add inside a lane ripples through its K words with the carry flag;
 //   * the lanes of a group run skewed by one row each (lane g works on row t - g at step t), so the carry out of a
-//     lane's 128 bits for a row is shuffled to the next lane, which adds it in the same row one step later;
-//   * a warp works on floor(32 / G) pairs of the same group size at once, G = ceil(ceil(n / 32) / 4) lanes per
-//     pair (so short pairs share a warp and long pairs spread over it).
-// The host plans the launch: it buckets pairs by G, orders work items (up to 32 / G pairs each) by decreasing
+//     lane's 32K bits for a row is shuffled to the next lane, which adds it in the same row one step later;
+//   * a warp works on floor(32 / G) pairs of the same shape at once, G = ceil(ceil(n / 32) / K) lanes per pair (so
+//     short pairs share a warp and long pairs spread over it).
+// The host plans the launch: it buckets pairs by (K, G), orders work items (up to 32 / G pairs each) by decreasing
 // rows, and a persistent kernel lets every warp take the next item from an atomic ticket. A pair with many rows is
 // split in two jobs that run at the same time, its top half forward and its bottom half on the reversed strings;
 // a small kernel then takes L = max_j (c[mt, j] + LCS(X[mt+1..m], Y[j+1..n])) from the two final rows, so the
-// longest serial chain of rows in a batch is halved.
+// longest serial chain of rows in a batch is halved. Words per lane, the height above which a pair is split and the
+// resident blocks per SM form the batch configuration, which lcs_ctx_autotune_batch_dev picks by timing.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -33,8 +34,7 @@ namespace {
 using namespace lcs;
 
 constexpr uint32_t kFull = 0xFFFFFFFFu;
-constexpr int kBK = 4;             // words per lane
-constexpr int kWarpWords = 32 * kBK;  // 128 words per warp row
+constexpr int kRowWords = 128;     // words of the longest row of a batch pair (n <= 4096)
 constexpr int kBatchWarps = 8;     // warps per block of the persistent kernel
 constexpr int kStageRows = 24;     // match-mask rows staged in shared memory per warp (alphabets up to 23 symbols)
 
@@ -55,8 +55,9 @@ struct BJob {         // the rows of one pair a group of lanes works through
   uint32_t pair, rev, rows, pad;
 };
 
-struct BItem {        // a warp's unit of work: jobs [first, first + count), G lanes each
-  uint32_t first, count, G, rows;
+struct BItem {        // a warp's unit of work: jobs [first, first + count), G lanes of K words each
+  uint32_t first, count, rows;
+  uint16_t G, K;
 };
 
 struct BatchArgs {
@@ -68,19 +69,20 @@ struct BatchArgs {
   uint32_t* sigma;     // per plan pair: symbols present in y (its zero row index)
   uint16_t* xcode;     // per job: the codes of its rows in its pair's alphabet (0..256); 16 zeros at the start
   uint32_t* peq;
-  uint32_t* fvbuf;     // final rows of split pairs' jobs, kWarpWords words per slot
+  uint32_t* fvbuf;     // final rows of split pairs' jobs, kRowWords words per slot
   uint64_t* out_lens;
   uint32_t* ticket;      // ticket[0]: items of k_batch_main, ticket[1]: pairs of k_batch_prep
   const uint32_t* split;  // plan indices of split pairs
   const uint32_t* prep_order;  // plan indices of all pairs, most prep work first
   uint32_t npairs, nitems, nsplit;
+  uint32_t stage_words;  // k_batch_main: words of match-mask stage per warp (dynamic shared memory)
 };
 
 // ---- per-pair alphabet, symbol codes and match-mask table (one warp per pair) ------------------------------------
 // Strings are read with 16-byte loads where their alignment allows (a forward job's 16-bit codes are placed so
 // that a 16-byte group of x maps to a 32-byte group of codes), and y is kept in shared memory for the alphabet
 // and the table build.
-constexpr uint32_t kMaxBatchCols = kWarpWords * 32;  // 4096: the longest y of a batch pair
+constexpr uint32_t kMaxBatchCols = kRowWords * 32;  // 4096: the longest y of a batch pair
 
 constexpr uint32_t kCodePadFront = 32;  // zero-row codes before a job's list: lanes run up to 31 rows behind
 constexpr uint32_t kCodePadBack = 8;    // and after it: the main kernel reads 8 rows at a time
@@ -282,38 +284,103 @@ __global__ void __launch_bounds__(256, 4) k_batch_prep(BatchArgs a) {
 }
 
 // ---- the persistent batch kernel --------------------------------------------------------------------------------
-// S = V + U + c over the lane's 128 bits, c = cin & 1 when take is all ones and 0 when take is 0 (cin is 0 or 1);
-// cout = carry out of the lane's top bit.
-__device__ __forceinline__ void add4c(const uint32_t (&v)[kBK], const uint32_t (&u)[kBK], uint32_t cin,
-                                      uint32_t take, uint32_t (&s)[kBK], uint32_t& cout) {
+// S = V + U + c over the lane's K words (s holds V on entry), c = cin & 1 when take is all ones and 0 when take is 0
+// (cin is 0 or 1); cout = carry out of the lane's top bit. One asm block per K keeps the carry flag between the words.
+template <int K>
+__device__ __forceinline__ void addc_words(const uint32_t (&u)[K], uint32_t cin, uint32_t take, uint32_t (&s)[K],
+                                           uint32_t& cout);
+template <>
+__device__ __forceinline__ void addc_words<2>(const uint32_t (&u)[2], uint32_t cin, uint32_t take, uint32_t (&s)[2],
+                                              uint32_t& cout) {
   asm("{\n\t"
       ".reg .u32 t;\n\t"
-      "add.cc.u32 t, %5, %14;\n\t"  // carry flag = cin when take = 0xFFFFFFFF, 0 when take = 0
-      "addc.cc.u32 %0, %6, %10;\n\t"
-      "addc.cc.u32 %1, %7, %11;\n\t"
-      "addc.cc.u32 %2, %8, %12;\n\t"
-      "addc.cc.u32 %3, %9, %13;\n\t"
+      "add.cc.u32 t, %3, %6;\n\t"  // carry flag = cin when take = 0xFFFFFFFF, 0 when take = 0
+      "addc.cc.u32 %0, %0, %4;\n\t"
+      "addc.cc.u32 %1, %1, %5;\n\t"
+      "addc.u32 %2, 0, 0;\n\t"
+      "}"
+      : "+r"(s[0]), "+r"(s[1]), "=r"(cout)
+      : "r"(cin), "r"(u[0]), "r"(u[1]), "r"(take));
+}
+template <>
+__device__ __forceinline__ void addc_words<4>(const uint32_t (&u)[4], uint32_t cin, uint32_t take, uint32_t (&s)[4],
+                                              uint32_t& cout) {
+  asm("{\n\t"
+      ".reg .u32 t;\n\t"
+      "add.cc.u32 t, %5, %10;\n\t"
+      "addc.cc.u32 %0, %0, %6;\n\t"
+      "addc.cc.u32 %1, %1, %7;\n\t"
+      "addc.cc.u32 %2, %2, %8;\n\t"
+      "addc.cc.u32 %3, %3, %9;\n\t"
       "addc.u32 %4, 0, 0;\n\t"
       "}"
-      : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(cout)
-      : "r"(cin), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(u[0]), "r"(u[1]), "r"(u[2]), "r"(u[3]),
+      : "+r"(s[0]), "+r"(s[1]), "+r"(s[2]), "+r"(s[3]), "=r"(cout)
+      : "r"(cin), "r"(u[0]), "r"(u[1]), "r"(u[2]), "r"(u[3]), "r"(take));
+}
+template <>
+__device__ __forceinline__ void addc_words<8>(const uint32_t (&u)[8], uint32_t cin, uint32_t take, uint32_t (&s)[8],
+                                              uint32_t& cout) {
+  asm("{\n\t"
+      ".reg .u32 t;\n\t"
+      "add.cc.u32 t, %9, %18;\n\t"
+      "addc.cc.u32 %0, %0, %10;\n\t"
+      "addc.cc.u32 %1, %1, %11;\n\t"
+      "addc.cc.u32 %2, %2, %12;\n\t"
+      "addc.cc.u32 %3, %3, %13;\n\t"
+      "addc.cc.u32 %4, %4, %14;\n\t"
+      "addc.cc.u32 %5, %5, %15;\n\t"
+      "addc.cc.u32 %6, %6, %16;\n\t"
+      "addc.cc.u32 %7, %7, %17;\n\t"
+      "addc.u32 %8, 0, 0;\n\t"
+      "}"
+      : "+r"(s[0]), "+r"(s[1]), "+r"(s[2]), "+r"(s[3]), "+r"(s[4]), "+r"(s[5]), "+r"(s[6]), "+r"(s[7]),
+        "=r"(cout)
+      : "r"(cin), "r"(u[0]), "r"(u[1]), "r"(u[2]), "r"(u[3]), "r"(u[4]), "r"(u[5]), "r"(u[6]), "r"(u[7]),
         "r"(take));
 }
 
+// K consecutive words from shared memory (8-byte aligned for K = 2, 16-byte aligned otherwise).
+template <int K>
+__device__ __forceinline__ void lds_words(const uint32_t* src, uint32_t (&P)[K]) {
+  if constexpr (K == 2) {
+    const uint2 q = *reinterpret_cast<const uint2*>(src);
+    P[0] = q.x;
+    P[1] = q.y;
+  } else {
+#pragma unroll
+    for (int h = 0; h < K / 4; ++h) {
+      const uint4 q = reinterpret_cast<const uint4*>(src)[h];
+      P[4 * h] = q.x;
+      P[4 * h + 1] = q.y;
+      P[4 * h + 2] = q.z;
+      P[4 * h + 3] = q.w;
+    }
+  }
+}
+template <int K>
+__device__ __forceinline__ void sts_words(uint32_t* dst, const uint32_t (&v)[K]) {
+  if constexpr (K == 2) {
+    *reinterpret_cast<uint2*>(dst) = make_uint2(v[0], v[1]);
+  } else {
+#pragma unroll
+    for (int h = 0; h < K / 4; ++h)
+      reinterpret_cast<uint4*>(dst)[h] = make_uint4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
+  }
+}
+
 // The rows of one item for one lane. STAGED: the masks come from the warp's shared stage (lane_stage points at this
-// lane's 4 words of row 0; row r is kWarpWords words further), else from the pair's table in L2. The masks of the
-// next step are loaded one step ahead, the symbol codes eight steps ahead.
-template <bool STAGED>
-__device__ __forceinline__ void run_rows(uint32_t (&V)[kBK], const uint32_t* lane_stage, const uint32_t* peq,
+// lane's K words of row 0; row r is 32K words further), else from the pair's table in L2. The masks of the next step
+// are loaded one step ahead, the symbol codes eight steps ahead.
+template <int K, bool STAGED>
+__device__ __forceinline__ void run_rows(uint32_t (&V)[K], const uint32_t* lane_stage, const uint32_t* peq,
                                          uint64_t tab, uint32_t w, uint32_t w0, bool has, const uint16_t* xp,
                                          uint32_t jend, uint32_t gl, uint32_t take, uint32_t steps) {
-  auto load_p = [&](uint32_t code, uint32_t (&P)[kBK]) {
+  auto load_p = [&](uint32_t code, uint32_t (&P)[K]) {
     if (STAGED) {
-      const uint4 q = *reinterpret_cast<const uint4*>(lane_stage + code * kWarpWords);
-      P[0] = q.x; P[1] = q.y; P[2] = q.z; P[3] = q.w;
+      lds_words<K>(lane_stage + code * (32u * K), P);
     } else {
 #pragma unroll
-      for (int k = 0; k < kBK; ++k) {
+      for (int k = 0; k < K; ++k) {
         const uint32_t q = w0 + k;
         P[k] = (has && q < w) ? __ldg(peq + tab + (uint64_t)code * w + q) : 0u;
       }
@@ -325,7 +392,7 @@ __device__ __forceinline__ void run_rows(uint32_t (&V)[kBK], const uint32_t* lan
     for (int b = 0; b < 8; ++b) c[b] = __ldg(xp + r0 + b);
   };
   uint32_t cin = 0;
-  uint32_t cq[8], nq[8], P[kBK], Pn[kBK];
+  uint32_t cq[8], nq[8], P[K], Pn[K];
   codes8(0, cq);
   load_p(cq[0], Pn);
   for (uint32_t t0 = 0; t0 < steps; t0 += 8) {
@@ -333,108 +400,129 @@ __device__ __forceinline__ void run_rows(uint32_t (&V)[kBK], const uint32_t* lan
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
 #pragma unroll
-      for (int k = 0; k < kBK; ++k) P[k] = Pn[k];
+      for (int k = 0; k < K; ++k) P[k] = Pn[k];
       load_p(b + 1 < 8 ? cq[b + 1 < 8 ? b + 1 : 0] : nq[0], Pn);  // the next step's masks, one step ahead
-      uint32_t U[kBK], S[kBK], cout;
+      uint32_t U[K], S[K], cout;
 #pragma unroll
-      for (int k = 0; k < kBK; ++k) U[k] = V[k] & P[k];
-      add4c(V, U, cin, take, S, cout);
+      for (int k = 0; k < K; ++k) {
+        U[k] = V[k] & P[k];
+        S[k] = V[k];
+      }
+      addc_words<K>(U, cin, take, S, cout);
       cin = __shfl_up_sync(kFull, cout, 1);
 #pragma unroll
-      for (int k = 0; k < kBK; ++k) V[k] = S[k] | (V[k] & ~P[k]);
+      for (int k = 0; k < K; ++k) V[k] = S[k] | (V[k] & ~P[k]);
     }
 #pragma unroll
     for (int b = 0; b < 8; ++b) cq[b] = nq[b];
   }
 }
 
+// One work item with K words per lane (K is uniform over the warp: it comes from the item).
+template <int K>
+__device__ __forceinline__ void run_item(const BatchArgs& a, const BItem& item, uint32_t* stage, uint32_t lane) {
+  const uint32_t G = item.G;
+  const uint32_t grp = lane / G, gl = lane % G;
+  const bool has = grp < item.count;
+  BJob job{};
+  BPair pr{};
+  uint32_t sig = 0;
+  if (has) {
+    job = a.jobs[item.first + grp];
+    pr = a.pairs[job.pair];
+    sig = a.sigma[job.pair];
+  }
+  const uint64_t tab = job.rev ? pr.peqr_off : pr.peq_off;
+  // lanes whose group has no job, or whose words lie beyond the pair's row, read the all-zero row / zero words
+  const uint32_t w0 = gl * K;  // first word of this lane within its pair's row
+  const uint32_t sig_max = __reduce_max_sync(kFull, has ? sig : 0u);
+  const bool staged = (sig_max + 1) * 32u * K <= a.stage_words;
+  if (staged) {
+    // stage rows 0..sig_max: warp-row layout [row][lane * K + k]; rows above a pair's sigma read as zero
+    __syncwarp();
+    for (uint32_t r = 0; r <= sig_max; ++r) {
+      uint32_t v[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const uint32_t q = w0 + k;
+        v[k] = (has && r <= sig && q < pr.w) ? a.peq[tab + (uint64_t)r * pr.w + q] : 0u;
+      }
+      sts_words<K>(&stage[r * 32u * K + lane * K], v);
+    }
+    __syncwarp();
+  }
+  // Lane gl of a group works on row t - gl at step t (a skew of one row per lane), so the carry out of its 32K
+  // bits for that row reaches lane gl + 1 by one shuffle, in time for the same row at step t + 1. Rows before 0
+  // or past the job read the zero-row codes around the job's list: a row without a match leaves V unchanged.
+  // xp[r] is the code of row r - kCodePadFront; lanes without a job read the zeros at the start of xcode (code 0,
+  // whose staged row is zero for them).
+  const uint16_t* xp = has ? a.xcode + (job.rev ? pr.xcr : pr.xcf) - kCodePadFront : a.xcode;
+  const uint32_t jend = has ? job.rows + kCodePadFront : 0u;  // rows from here on read the padding only
+  const uint32_t take = gl ? kFull : 0u;  // the first lane of a group starts every row without a carry
+  const uint32_t steps = (item.rows + G - 1 + 7) & ~7u;
+  uint32_t V[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) V[k] = kFull;
+  if (staged)
+    run_rows<K, true>(V, stage + lane * K, a.peq, tab, pr.w, w0, has, xp, jend, gl, take, steps);
+  else
+    run_rows<K, false>(V, stage + lane * K, a.peq, tab, pr.w, w0, has, xp, jend, gl, take, steps);
+  if (has && pr.mt < pr.m) {
+    // a split pair: keep the job's final row for the combine kernel (words gl*K .. gl*K+K-1 < kRowWords)
+    uint32_t* dst = a.fvbuf + (uint64_t)(pr.fv + job.rev) * kRowWords + w0;
+    if constexpr (K == 2) {
+      *reinterpret_cast<uint2*>(dst) = make_uint2(V[0], V[1]);
+    } else {
+#pragma unroll
+      for (int h = 0; h < K / 4; ++h)
+        reinterpret_cast<uint4*>(dst)[h] = make_uint4(V[4 * h], V[4 * h + 1], V[4 * h + 2], V[4 * h + 3]);
+    }
+  } else if (has) {
+    // c[m, n] = zero bits of V over the pair's n columns (bits past n stay 1): every lane of the group adds its
+    // share to the length, which starts at zero
+    uint32_t z = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) z += __popc(~V[k]);
+    if (z) atomicAdd(reinterpret_cast<unsigned long long*>(a.out_lens + pr.out), (unsigned long long)z);
+  }
+}
+
 __global__ void __launch_bounds__(kBatchWarps * 32) k_batch_main(BatchArgs a) {
-  __shared__ __align__(16) uint32_t stage_s[kBatchWarps][kStageRows * kWarpWords];
+  extern __shared__ __align__(16) uint32_t stage_dyn[];  // [kBatchWarps][stage_words]
   const uint32_t wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint32_t* stage = stage_s[wid];
+  uint32_t* stage = stage_dyn + wid * a.stage_words;
   for (;;) {
     uint32_t it = 0;
     if (lane == 0) it = atomicAdd(a.ticket, 1u);
     it = __shfl_sync(kFull, it, 0);
     if (it >= a.nitems) break;
     const BItem item = a.items[it];
-    const uint32_t G = item.G;
-    const uint32_t grp = lane / G, gl = lane % G;
-    const bool has = grp < item.count;
-    BJob job{};
-    BPair pr{};
-    uint32_t sig = 0;
-    if (has) {
-      job = a.jobs[item.first + grp];
-      pr = a.pairs[job.pair];
-      sig = a.sigma[job.pair];
-    }
-    const uint64_t tab = job.rev ? pr.peqr_off : pr.peq_off;
-    // lanes whose group has no job, or whose words lie beyond the pair's row, read the all-zero row / zero words
-    const uint32_t w0 = gl * kBK;  // first word of this lane within its pair's row
-    uint32_t sig_max = __reduce_max_sync(kFull, has ? sig : 0u);
-    const bool staged = sig_max + 1 <= (uint32_t)kStageRows;
-    if (staged) {
-      // stage rows 0..sig_max: warp-row layout [row][lane * 4 + k]; rows above a pair's sigma read as zero
-      __syncwarp();
-      for (uint32_t r = 0; r <= sig_max; ++r) {
-        uint32_t v[kBK];
-#pragma unroll
-        for (int k = 0; k < kBK; ++k) {
-          const uint32_t q = w0 + k;
-          v[k] = (has && r <= sig && q < pr.w) ? a.peq[tab + (uint64_t)r * pr.w + q] : 0u;
-        }
-        *reinterpret_cast<uint4*>(&stage[r * kWarpWords + lane * kBK]) = make_uint4(v[0], v[1], v[2], v[3]);
-      }
-      __syncwarp();
-    }
-    // Lane gl of a group works on row t - gl at step t (a skew of one row per lane), so the carry out of its 128
-    // bits for that row reaches lane gl + 1 by one shuffle, in time for the same row at step t + 1. Rows before 0
-    // or past the job read the zero-row codes around the job's list: a row without a match leaves V unchanged.
-    // xp[r] is the code of row r - kCodePadFront; lanes without a job read the zeros at the start of xcode (code 0,
-    // whose staged row is zero for them).
-    const uint16_t* xp = has ? a.xcode + (job.rev ? pr.xcr : pr.xcf) - kCodePadFront : a.xcode;
-    const uint32_t jend = has ? job.rows + kCodePadFront : 0u;  // rows from here on read the padding only
-    const uint32_t take = gl ? kFull : 0u;  // the first lane of a group starts every row without a carry
-    const uint32_t steps = (item.rows + G - 1 + 7) & ~7u;
-    uint32_t V[kBK] = {kFull, kFull, kFull, kFull};
-    if (staged)
-      run_rows<true>(V, stage + lane * kBK, a.peq, tab, pr.w, w0, has, xp, jend, gl, take, steps);
-    else
-      run_rows<false>(V, stage + lane * kBK, a.peq, tab, pr.w, w0, has, xp, jend, gl, take, steps);
-    if (has && pr.mt < pr.m) {
-      // a split pair: keep the job's final row for the combine kernel
-      uint4* dst = reinterpret_cast<uint4*>(a.fvbuf + (uint64_t)(pr.fv + job.rev) * kWarpWords + gl * kBK);
-      *dst = make_uint4(V[0], V[1], V[2], V[3]);
-    } else if (has) {
-      // c[m, n] = zero bits of V over the pair's n columns (bits past n stay 1): every lane of the group adds its
-      // share to the length, which starts at zero
-      uint32_t z = 0;
-#pragma unroll
-      for (int k = 0; k < kBK; ++k) z += __popc(~V[k]);
-      if (z) atomicAdd(reinterpret_cast<unsigned long long*>(a.out_lens + pr.out), (unsigned long long)z);
-    }
+    if (item.K == 8) run_item<8>(a, item, stage, lane);
+    else if (item.K == 2) run_item<2>(a, item, stage, lane);
+    else run_item<4>(a, item, stage, lane);
   }
 }
 
 // Split pairs: L = n - min over j of (ones of the forward row among its first j columns + ones of the reverse row
 // among its first n - j columns). One warp per pair, prefix popcounts of the two rows in shared memory.
+constexpr int kCW = kRowWords / 32;  // words of a final row per lane in the combine kernel
+
 __global__ void __launch_bounds__(256) k_batch_combine(BatchArgs a) {
-  __shared__ uint32_t pre_s[8][2][kWarpWords + 1];  // ones among the first 32q columns, q = 0..128
-  __shared__ uint32_t row_s[8][2][kWarpWords];
+  __shared__ uint32_t pre_s[8][2][kRowWords + 1];  // ones among the first 32q columns, q = 0..128
+  __shared__ uint32_t row_s[8][2][kRowWords];
   const uint32_t wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
   for (uint32_t k = blockIdx.x * (blockDim.x >> 5) + wid; k < a.nsplit; k += nwarps) {
     const BPair pr = a.pairs[a.split[k]];
     for (int d = 0; d < 2; ++d) {
-      const uint4 v4 = *reinterpret_cast<const uint4*>(a.fvbuf + (uint64_t)(pr.fv + d) * kWarpWords + lane * kBK);
-      const uint32_t v[kBK] = {v4.x, v4.y, v4.z, v4.w};
-      uint32_t c[kBK], sum = 0;
+      const uint4 v4 = *reinterpret_cast<const uint4*>(a.fvbuf + (uint64_t)(pr.fv + d) * kRowWords + lane * kCW);
+      const uint32_t v[kCW] = {v4.x, v4.y, v4.z, v4.w};
+      uint32_t c[kCW], sum = 0;
 #pragma unroll
-      for (int q = 0; q < kBK; ++q) {
+      for (int q = 0; q < kCW; ++q) {
         c[q] = __popc(v[q]);
         sum += c[q];
-        row_s[wid][d][lane * kBK + q] = v[q];
+        row_s[wid][d][lane * kCW + q] = v[q];
       }
       uint32_t incl = sum;
       for (uint32_t off = 1; off < 32; off <<= 1) {
@@ -443,11 +531,11 @@ __global__ void __launch_bounds__(256) k_batch_combine(BatchArgs a) {
       }
       uint32_t run = incl - sum;
 #pragma unroll
-      for (int q = 0; q < kBK; ++q) {
-        pre_s[wid][d][lane * kBK + q] = run;
+      for (int q = 0; q < kCW; ++q) {
+        pre_s[wid][d][lane * kCW + q] = run;
         run += c[q];
       }
-      if (lane == 31) pre_s[wid][d][kWarpWords] = incl;
+      if (lane == 31) pre_s[wid][d][kRowWords] = incl;
     }
     __syncwarp();
     auto ones = [&](int d, uint32_t x) {
@@ -465,8 +553,16 @@ __global__ void __launch_bounds__(256) k_batch_combine(BatchArgs a) {
   }
 }
 
-// Lanes per pair: just enough to hold its words, 4 per lane (so 32 / G pairs share a warp).
-inline uint32_t group_lanes(uint32_t w) { return w == 0 ? 1u : (w + kBK - 1) / kBK; }
+// Lanes per pair: just enough to hold its w words at K per lane (so 32 / G pairs share a warp).
+inline uint32_t group_lanes(uint32_t w, uint32_t K) { return w == 0 ? 1u : (w + K - 1) / K; }
+
+// Words per lane of a pair with w words per row: the configured K, or the smallest larger one that fits the row in
+// one warp (32 lanes).
+inline uint32_t lane_words(uint32_t w, uint32_t k_cfg) {
+  uint32_t K = k_cfg;
+  while (K < 8 && w > 32 * K) K *= 2;
+  return K;
+}
 
 struct Plan {
   std::vector<BPair> pairs;
@@ -477,27 +573,31 @@ struct Plan {
   uint64_t peq_words = 0;
   uint64_t codes = kCodeZeros;  // xcode: zeros, then the jobs' padded code lists
   uint32_t fv_slots = 0;
+  uint32_t k_max = 2;  // the largest words per lane of an item (sizes the kernel's mask stage)
 };
 
 constexpr uint32_t kSplitMinRows = 256;  // pairs with fewer rows are never split
 
 // Host plan: lengths from the offsets; pairs whose words exceed one warp's 128 (n > 4096) are not handled here.
-// A pair is split when its rows exceed both kSplitMinRows and the rows an average resident warp works through
-// (the batch's lane-rows spread over `warps`), i.e. when its serial chain would outlast the rest of the launch.
-bool make_plan(const uint64_t* x_off, const uint64_t* y_off, uint64_t count, uint64_t warps, Plan& plan,
-               std::vector<uint64_t>& big) {
+// A pair is split when its rows exceed both kSplitMinRows and split_pct % of the rows an average resident warp
+// works through (the batch's lane-rows spread over `warps`), i.e. when its serial chain would outlast the rest of
+// the launch; split_pct = 0 never splits. k_cfg is the configured words per lane.
+bool make_plan(const uint64_t* x_off, const uint64_t* y_off, uint64_t count, uint64_t warps, uint32_t k_cfg,
+               uint32_t split_pct, Plan& plan, std::vector<uint64_t>& big) {
   uint64_t lane_rows = 0;
   for (uint64_t k = 0; k < count; ++k) {
     const uint64_t m = x_off[k + 1] - x_off[k], n = y_off[k + 1] - y_off[k];
     const uint64_t w = (n + 31) / 32;
-    if (m && n && w <= (uint64_t)kWarpWords) lane_rows += m * group_lanes((uint32_t)w);
+    if (m && n && w <= (uint64_t)kRowWords) lane_rows += m * group_lanes((uint32_t)w, lane_words((uint32_t)w, k_cfg));
   }
-  const uint64_t split_rows = std::max<uint64_t>(kSplitMinRows, lane_rows / (32 * std::max<uint64_t>(warps, 1)));
+  const uint64_t avg_rows = lane_rows / (32 * std::max<uint64_t>(warps, 1));
+  const uint64_t split_rows =
+      split_pct ? std::max<uint64_t>(kSplitMinRows, avg_rows * split_pct / 100) : ~(uint64_t)0;
   for (uint64_t k = 0; k < count; ++k) {
     const uint64_t m = x_off[k + 1] - x_off[k], n = y_off[k + 1] - y_off[k];
     if (m == 0 || n == 0) continue;  // length 0, written by the zeroing launch
     const uint64_t w = (n + 31) / 32;
-    if (w > (uint64_t)kWarpWords || m >= (1ull << 31)) {
+    if (w > (uint64_t)kRowWords || m >= (1ull << 31)) {
       big.push_back(k);
       continue;
     }
@@ -540,27 +640,38 @@ bool make_plan(const uint64_t* x_off, const uint64_t* y_off, uint64_t count, uin
   };
   std::stable_sort(plan.prep_order.begin(), plan.prep_order.end(),
                    [&](uint32_t u, uint32_t v) { return prep_cost(u) > prep_cost(v); });
-  // bucket jobs by G; within a bucket, longest first (similar rows share a warp)
-  std::vector<uint32_t> G(plan.jobs.size());
-  for (size_t j = 0; j < plan.jobs.size(); ++j) G[j] = group_lanes(plan.pairs[plan.jobs[j].pair].w);
+  // bucket jobs by (G, K); within a bucket, longest first (similar rows share a warp)
+  std::vector<uint32_t> K(plan.jobs.size()), G(plan.jobs.size());
+  for (size_t j = 0; j < plan.jobs.size(); ++j) {
+    const uint32_t w = plan.pairs[plan.jobs[j].pair].w;
+    K[j] = lane_words(w, k_cfg);
+    G[j] = group_lanes(w, K[j]);
+  }
   std::vector<uint32_t> order(plan.jobs.size());
   std::iota(order.begin(), order.end(), 0u);
   std::sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) {
     if (G[a] != G[b]) return G[a] > G[b];
+    if (K[a] != K[b]) return K[a] > K[b];
     return plan.jobs[a].rows > plan.jobs[b].rows;
   });
   std::vector<BJob> jobs(order.size());
-  for (size_t j = 0; j < order.size(); ++j) jobs[j] = plan.jobs[order[j]];
+  std::vector<uint32_t> Ks(order.size()), Gs(order.size());
+  for (size_t j = 0; j < order.size(); ++j) {
+    jobs[j] = plan.jobs[order[j]];
+    Ks[j] = K[order[j]];
+    Gs[j] = G[order[j]];
+  }
   plan.jobs.swap(jobs);
   for (size_t i = 0; i < plan.jobs.size();) {
-    const uint32_t g = group_lanes(plan.pairs[plan.jobs[i].pair].w), per = 32 / g;
+    const uint32_t g = Gs[i], kk = Ks[i], per = 32 / g;
     size_t j = i;
     uint32_t rows = 0;
-    while (j < plan.jobs.size() && j - i < per && group_lanes(plan.pairs[plan.jobs[j].pair].w) == g) {
+    while (j < plan.jobs.size() && j - i < per && Gs[j] == g && Ks[j] == kk) {
       rows = std::max(rows, plan.jobs[j].rows);
       ++j;
     }
-    plan.items.push_back({(uint32_t)i, (uint32_t)(j - i), g, rows});
+    plan.items.push_back({(uint32_t)i, (uint32_t)(j - i), rows, (uint16_t)g, (uint16_t)kk});
+    plan.k_max = std::max(plan.k_max, kk);
     i = j;
   }
   // longest items first: an item holds its warp for rows + G - 1 steps whatever its G (list scheduling by the
@@ -576,29 +687,44 @@ namespace lcs {
 int run_length(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, uint64_t n, uint64_t* d_out,
                cudaStream_t st);
 
-// Resident blocks of the persistent row kernel per SM: one (8 warps, two per scheduler) unless
-// LCS_BATCH_BLOCKS_PER_SM asks for more, up to the occupancy limit. The ALU work of the bulk of the items keeps
-// two warps per scheduler busy, and the longest items, whose serial chains of rows end the launch, then share
-// their schedulers with one other warp instead of three (measured: 0.180 ms against 0.201 ms with two blocks
-// for the 10000-pair workload). The split of long pairs still assumes the occupancy limit, so that items stay
-// short.
+// Shared memory of the persistent row kernel: a stage of kStageRows mask rows of 32 * k_max words per warp.
+inline uint32_t stage_words_for(uint32_t k_max) { return (uint32_t)kStageRows * 32u * k_max; }
+inline size_t main_smem_bytes(uint32_t k_max) { return (size_t)kBatchWarps * stage_words_for(k_max) * 4u; }
+inline int k_index(uint32_t k) { return k >= 8 ? 2 : (k >= 4 ? 1 : 0); }
+
+// Resident blocks of the persistent row kernel per SM: the configured number (one by default: 8 warps, two per
+// scheduler), up to the occupancy limit of the plan's stage size. The ALU work of the bulk of the items keeps two
+// warps per scheduler busy, and the longest items, whose serial chains of rows end the launch, then share their
+// schedulers with one other warp instead of three (measured: 0.180 ms against 0.201 ms with two blocks for the
+// 10000-pair workload). The split of long pairs assumes the occupancy limit at 4 words per lane, so that items
+// stay short.
 static int batch_blocks_per_sm(lcs_ctx* c, int occ) {
   const int want = c->batch_blocks_per_sm > 0 ? c->batch_blocks_per_sm : 1;
   return want < occ ? want : occ;
 }
 
-// Device facts the batch launches need, looked up once per context.
+// Device facts the batch launches need, looked up once per context: SMs, prep occupancy, and the row kernel's
+// occupancy for each stage size (largest words per lane 2, 4, 8).
 static cudaError_t batch_geometry(lcs_ctx* c) {
   if (c->b_sms > 0) return cudaSuccess;
-  int sms = 0, prep_per_sm = 0, main_per_sm = 0;
-  cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  static std::atomic<uint64_t> attr_done{0};
+  cudaError_t e = once_per_device_attr(
+      [] {
+        return cudaFuncSetAttribute(k_batch_main, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)main_smem_bytes(8));
+      },
+      attr_done);
+  int sms = 0, prep_per_sm = 0, occ[3] = {0, 0, 0};
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&prep_per_sm, k_batch_prep, 256, 0);
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&main_per_sm, k_batch_main, kBatchWarps * 32, 0);
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[i], k_batch_main, kBatchWarps * 32,
+                                                      main_smem_bytes(2u << i));
   if (e != cudaSuccess) return e;
   c->b_sms = std::max(sms, 1);
   c->b_prep_per_sm = std::max(prep_per_sm, 1);
-  c->b_main_occ = std::max(main_per_sm, 1);
+  for (int i = 0; i < 3; ++i) c->b_main_occ_k[i] = std::max(occ[i], 1);
+  c->b_main_occ = c->b_main_occ_k[1];
   return cudaSuccess;
 }
 
@@ -615,9 +741,10 @@ static cudaError_t batch_launches(lcs_ctx* c, uint64_t* d_out, uint64_t count, c
     const uint64_t sms = (uint64_t)c->b_sms;
     const unsigned prep_blocks = (unsigned)std::min<uint64_t>((a.npairs + 7) / 8, sms * c->b_prep_per_sm);
     k_batch_prep<<<prep_blocks, 256, 0, st>>>(a);
-    const unsigned blocks = (unsigned)(sms * batch_blocks_per_sm(c, c->b_main_occ));
+    const uint32_t k_max = a.stage_words / (32u * kStageRows);
+    const unsigned blocks = (unsigned)(sms * batch_blocks_per_sm(c, c->b_main_occ_k[k_index(k_max)]));
     if (marks) c->mark(1, st);
-    k_batch_main<<<blocks, kBatchWarps * 32, 0, st>>>(a);
+    k_batch_main<<<blocks, kBatchWarps * 32, main_smem_bytes(k_max), st>>>(a);
     if (a.nsplit) k_batch_combine<<<(unsigned)std::min<uint64_t>((a.nsplit + 7) / 8, sms * 8), 256, 0, st>>>(a);
     if (marks) c->mark(2, st);
     c->bblocks = blocks;
@@ -649,7 +776,9 @@ int run_batch(lcs_ctx* c, const uint8_t* d_xs, const uint8_t* d_ys, const uint64
     c->bbig.clear();
     rc = from_cuda(batch_geometry(c));
     if (rc) return rc;
-    make_plan(x_off, y_off, count, (uint64_t)c->b_sms * c->b_main_occ * kBatchWarps, plan, c->bbig);
+    make_plan(x_off, y_off, count, (uint64_t)c->b_sms * c->b_main_occ * kBatchWarps, c->batch_k, c->batch_split_pct,
+              plan, c->bbig);
+    c->bk_max = plan.k_max;
     c->bcells = 0;
     for (uint64_t k = 0; k < count; ++k) c->bcells += (x_off[k + 1] - x_off[k]) * (y_off[k + 1] - y_off[k]);
     const size_t pb = plan.pairs.size() * sizeof(BPair), jb = plan.jobs.size() * sizeof(BJob),
@@ -662,7 +791,7 @@ int run_batch(lcs_ctx* c, const uint8_t* d_xs, const uint8_t* d_ys, const uint64
       if (!rc) rc = from_cuda(ensure(c->bsig, plan.pairs.size() * 4 + 4));
       if (!rc) rc = from_cuda(ensure(c->bxcode, (plan.codes + 16) * 2));
       if (!rc) rc = from_cuda(ensure(c->bpeq, plan.peq_words * 4 + 4));
-      if (!rc) rc = from_cuda(ensure(c->bfv, ((uint64_t)plan.fv_slots * kWarpWords + 4) * 4));
+      if (!rc) rc = from_cuda(ensure(c->bfv, ((uint64_t)plan.fv_slots * kRowWords + 4) * 4));
       if (rc) return rc;
       // (copies from pageable memory: the runtime has staged the data when the call returns)
       char* base = (char*)c->bplan.p;
@@ -706,6 +835,7 @@ int run_batch(lcs_ctx* c, const uint8_t* d_xs, const uint8_t* d_ys, const uint64
   a.npairs = (uint32_t)c->bnpairs;
   a.nitems = (uint32_t)c->bnitems;
   a.nsplit = (uint32_t)c->bnsplit;
+  a.stage_words = stage_words_for(c->bk_max);
   if (c->prof || fresh) {
     rc = from_cuda(batch_launches(c, d_out, count, a, st, c->prof));
   } else {
@@ -825,6 +955,129 @@ extern "C" int lcs_batch(lcs_ctx* c, const uint8_t* xs, const uint64_t* x_off, c
                          const uint64_t* y_off, uint64_t count, uint64_t* out_lens) {
   try {  // no C++ exception crosses the C boundary
     return lcs_batch_impl(c, xs, x_off, ys, y_off, count, out_lens);
+  } catch (const std::bad_alloc&) {
+    return LCS_ERR_NOMEM;
+  } catch (...) {
+    return LCS_ERR_INTERNAL;
+  }
+}
+
+// ---- batch configuration and autotuning ---------------------------------------------------------------------------
+
+static bool valid_batch_config(const lcs_batch_config* b) {
+  return b && (b->words_per_lane == 2 || b->words_per_lane == 4 || b->words_per_lane == 8) && b->split_pct <= 1000 &&
+         (b->blocks_per_sm == 1 || b->blocks_per_sm == 2) && b->reserved == 0;
+}
+
+static lcs_batch_config current_batch_config(const lcs_ctx* c) {
+  lcs_batch_config b{};
+  b.words_per_lane = c->batch_k;
+  b.split_pct = c->batch_split_pct;
+  b.blocks_per_sm = c->batch_blocks_per_sm > 1 ? 2u : 1u;
+  return b;
+}
+
+static void apply_batch_config(lcs_ctx* c, const lcs_batch_config& b) {
+  if (b.words_per_lane != c->batch_k || b.split_pct != c->batch_split_pct) c->bvalid = false;  // re-plan
+  if ((int)b.blocks_per_sm != (c->batch_blocks_per_sm > 1 ? 2 : 1)) c->bvalid = false;  // re-capture the launches
+  c->batch_k = b.words_per_lane;
+  c->batch_split_pct = b.split_pct;
+  c->batch_blocks_per_sm = (int)b.blocks_per_sm;
+}
+
+extern "C" int lcs_ctx_get_batch_config(lcs_ctx* c, lcs_batch_config* out) {
+  if (!c || !out) return LCS_ERR_INVALID;
+  std::lock_guard<std::mutex> g(c->mu);
+  *out = current_batch_config(c);
+  return LCS_OK;
+}
+
+extern "C" int lcs_ctx_set_batch_config(lcs_ctx* c, const lcs_batch_config* cfg) {
+  if (!c || !valid_batch_config(cfg)) return LCS_ERR_INVALID;
+  std::lock_guard<std::mutex> g(c->mu);
+  apply_batch_config(c, *cfg);
+  return LCS_OK;
+}
+
+static int autotune_batch_impl(lcs_ctx* c, const uint8_t* d_xs, const uint64_t* d_x_off, const uint8_t* d_ys,
+                               const uint64_t* d_y_off, uint64_t count, uint64_t* d_out, void* stream,
+                               lcs_batch_config* best, double* best_ms) {
+  if (!c || (count && (!d_x_off || !d_y_off || !d_out))) return LCS_ERR_INVALID;
+  std::lock_guard<std::mutex> g(c->mu);
+  cudaSetDevice(c->device);
+  cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
+  const lcs_batch_config keep = current_batch_config(c);
+  if (count == 0) {
+    if (best) *best = keep;
+    if (best_ms) *best_ms = 0.0;
+    return LCS_OK;
+  }
+  std::vector<uint64_t> xo(count + 1), yo(count + 1);
+  int rc = from_cuda(cudaMemcpyAsync(xo.data(), d_x_off, (count + 1) * 8, cudaMemcpyDeviceToHost, st));
+  if (!rc) rc = from_cuda(cudaMemcpyAsync(yo.data(), d_y_off, (count + 1) * 8, cudaMemcpyDeviceToHost, st));
+  if (!rc) rc = from_cuda(cudaStreamSynchronize(st));
+  if (rc) return rc;
+  if (!offsets_ok(xo.data(), count) || !offsets_ok(yo.data(), count)) return LCS_ERR_INVALID;
+  const bool prof = c->prof;
+  c->prof = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  rc = from_cuda(cudaEventCreate(&e0));
+  if (!rc) rc = from_cuda(cudaEventCreate(&e1));
+  std::vector<uint64_t> first(count), now(count);
+  bool have_first = false;
+  double bt = 1e300;
+  lcs_batch_config bc = keep;
+  const uint32_t ks[3] = {2, 4, 8}, splits[4] = {50, 100, 200, 0}, bps[2] = {1, 2};
+  for (uint32_t k : ks) {
+    for (uint32_t sp : splits) {
+      for (uint32_t bp : bps) {
+        if (rc) break;
+        const lcs_batch_config cand{k, sp, bp, 0};
+        apply_batch_config(c, cand);
+        double ts[5];
+        for (int r = 0; r < 5 && !rc; ++r) {  // call 0 plans, call 1 captures the graph; calls 2-4 replay it
+          rc = from_cuda(cudaEventRecord(e0, st));
+          if (!rc) rc = run_batch(c, d_xs + xo[0], d_ys + yo[0], xo.data(), yo.data(), count, d_out, st);
+          if (!rc) rc = from_cuda(cudaEventRecord(e1, st));
+          if (!rc) rc = from_cuda(cudaEventSynchronize(e1));
+          if (!rc) rc = take_status(c);
+          float ms = 0.f;
+          if (!rc) rc = from_cuda(cudaEventElapsedTime(&ms, e0, e1));
+          ts[r] = ms;
+        }
+        if (rc) break;
+        // every configuration must give the same lengths
+        rc = from_cuda(cudaMemcpy((have_first ? now : first).data(), d_out, count * 8, cudaMemcpyDeviceToHost));
+        if (rc) break;
+        if (have_first && std::memcmp(first.data(), now.data(), count * 8) != 0) {
+          rc = LCS_ERR_INTERNAL;
+          break;
+        }
+        have_first = true;
+        std::sort(ts + 2, ts + 5);
+        if (ts[3] < bt) {
+          bt = ts[3];
+          bc = cand;
+        }
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  c->prof = prof;
+  apply_batch_config(c, rc ? keep : bc);
+  if (rc) return rc;
+  if (best) *best = bc;
+  if (best_ms) *best_ms = bt;
+  return LCS_OK;
+}
+
+extern "C" int lcs_ctx_autotune_batch_dev(lcs_ctx* c, const uint8_t* d_xs, const uint64_t* d_x_off,
+                                          const uint8_t* d_ys, const uint64_t* d_y_off, uint64_t count,
+                                          uint64_t* d_out_lens, void* stream, lcs_batch_config* best,
+                                          double* best_ms) {
+  try {  // no C++ exception crosses the C boundary
+    return autotune_batch_impl(c, d_xs, d_x_off, d_ys, d_y_off, count, d_out_lens, stream, best, best_ms);
   } catch (const std::bad_alloc&) {
     return LCS_ERR_NOMEM;
   } catch (...) {

@@ -41,7 +41,12 @@ struct lcs_ctx {
   uint32_t fill_variant = 0;     // length-only fills: bits 1-2 select the hand-off validation group (see launch_fill)
   uint32_t fill_variant_tb = 0;  // the same for traceback fills
   int b_sms = 0, b_prep_per_sm = 0, b_main_occ = 0;  // batch: SMs and blocks per SM (looked up once)
-  int batch_blocks_per_sm = 0;  // persistent batch kernel blocks per SM (0 = one)
+  int b_main_occ_k[3] = {0, 0, 0};  // batch row kernel: blocks per SM at the stage sizes of 2 / 4 / 8 words per lane
+  // batch configuration (lcs_ctx_set_batch_config): words per lane, split height in % of the average rows per
+  // resident warp (0 = never split), persistent kernel blocks per SM (0 = one)
+  uint32_t batch_k = 4, batch_split_pct = 100;
+  int batch_blocks_per_sm = 0;
+  uint32_t bk_max = 4;  // the planned batch's largest words per lane
   uint32_t debug_drop = 0;    // test hook (environment LCS_DEBUG_DROP_HANDOFF): a hand-off that never comes
   std::mutex mu;
   lcs::DBuf small, x, y, out;

@@ -25,7 +25,7 @@ EXPORTS = (
     "lcs_traceback", "lcs_traceback_dev", "lcs_batch", "lcs_batch_dev", "lcs_serve_create", "lcs_serve_submit",
     "lcs_serve_poll", "lcs_serve_wait", "lcs_result_release", "lcs_serve_destroy", "lcs_ctx_set_profiling",
     "lcs_ctx_last_profile", "lcs_tables", "lcs_tables_dev", "lcs_ctx_get_fill_config", "lcs_ctx_set_fill_config",
-    "lcs_ctx_autotune_dev",
+    "lcs_ctx_autotune_dev", "lcs_ctx_get_batch_config", "lcs_ctx_set_batch_config", "lcs_ctx_autotune_batch_dev",
 )
 
 
@@ -47,6 +47,11 @@ class Profile(ctypes.Structure):
 
 class FillConfig(ctypes.Structure):
     _fields_ = [("rows_per_step", ctypes.c_uint32), ("vg_select", ctypes.c_uint32)]
+
+
+class BatchConfig(ctypes.Structure):
+    _fields_ = [("words_per_lane", ctypes.c_uint32), ("split_pct", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
 
 
 class Result(ctypes.Structure):
@@ -86,6 +91,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lcs_ctx_set_fill_config": (ctypes.c_int, [vp, u32, ctypes.POINTER(FillConfig)]),
         "lcs_ctx_autotune_dev": (ctypes.c_int, [vp, vp, u64, vp, u64, u32, vp, ctypes.POINTER(FillConfig),
                                                  ctypes.POINTER(ctypes.c_double)]),
+        "lcs_ctx_get_batch_config": (ctypes.c_int, [vp, ctypes.POINTER(BatchConfig)]),
+        "lcs_ctx_set_batch_config": (ctypes.c_int, [vp, ctypes.POINTER(BatchConfig)]),
+        "lcs_ctx_autotune_batch_dev": (ctypes.c_int, [vp, vp, vp, vp, vp, u64, vp, vp, ctypes.POINTER(BatchConfig),
+                                                       ctypes.POINTER(ctypes.c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -181,6 +190,28 @@ class Context:
                                        ctypes.byref(ms))
         _check(rc, "lcs_ctx_autotune_dev")
         return {"rows_per_step": f.rows_per_step, "vg_select": f.vg_select, "ms": ms.value}
+
+    def get_batch_config(self) -> dict:
+        b = BatchConfig()
+        _check(_lib.lcs_ctx_get_batch_config(self._h, ctypes.byref(b)), "lcs_ctx_get_batch_config")
+        return {"words_per_lane": b.words_per_lane, "split_pct": b.split_pct, "blocks_per_sm": b.blocks_per_sm}
+
+    def set_batch_config(self, words_per_lane: int = 4, split_pct: int = 100, blocks_per_sm: int = 1) -> None:
+        b = BatchConfig(words_per_lane, split_pct, blocks_per_sm, 0)
+        _check(_lib.lcs_ctx_set_batch_config(self._h, ctypes.byref(b)), "lcs_ctx_set_batch_config")
+
+    def autotune_batch_dev(self, xs, x_off, ys, y_off, count: int, out, stream=None) -> dict:
+        """Times every batch configuration on the batch given as for batch_dev and keeps the fastest
+        (lcs_ctx_autotune_batch_dev); out receives the lengths."""
+        b = BatchConfig()
+        ms = ctypes.c_double(0.0)
+        rc = _lib.lcs_ctx_autotune_batch_dev(self._h, ctypes.c_void_p(xs.data_ptr()), ctypes.c_void_p(x_off.data_ptr()),
+                                             ctypes.c_void_p(ys.data_ptr()), ctypes.c_void_p(y_off.data_ptr()), count,
+                                             ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream), ctypes.byref(b),
+                                             ctypes.byref(ms))
+        _check(rc, "lcs_ctx_autotune_batch_dev")
+        return {"words_per_lane": b.words_per_lane, "split_pct": b.split_pct, "blocks_per_sm": b.blocks_per_sm,
+                "ms": ms.value}
 
     # -- host buffers -------------------------------------------------------------------------------------------
     def length(self, x, y) -> int:
