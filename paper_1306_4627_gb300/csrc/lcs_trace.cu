@@ -13,6 +13,7 @@
 // entry is the exit of the segment below (or walking the segment itself when the corridor had more columns than
 // walkers). The chosen walkers' symbols are finally copied to the output in order. The result is exactly the walk
 // of Print-LCS; only the order of the work differs.
+#include <algorithm>
 #include <atomic>
 
 #include "lcs_internal.h"
@@ -22,6 +23,7 @@ namespace lcs {
 namespace {
 
 constexpr uint32_t kFull = 0xFFFFFFFFu;
+constexpr uint64_t kWarpWalkers = 32;  // corridors of up to this many columns get a warp per walker
 
 // ---- word prefix popcounts of V rows ------------------------------------------------------------------------
 // For a V row (bit j-1 of the row = 1 - (c[i,j] - c[i,j-1])), pre[q] = ones among the first 32*q bits.
@@ -155,7 +157,13 @@ __global__ void k_corr_cols(TraceArgs a) {
   const uint64_t xb = a.n - j0;                      // the reverse position of column j0 (the largest)
   const uint64_t qb = xb >> 5;
   const uint64_t qa = xb >= 31 ? (xb - 31) >> 5 : 0; // the word of the smallest position used
-  const uint32_t bra = pr[qa], wra = vr[qa], brb = pr[qb], wrb = qb < a.w ? vr[qb] : 0u;
+  const uint32_t bra = pr[qa], wra = vr[qa];
+  // Over the thread's columns, ones_f(j) never falls below its value at j0 (bf) and ones_r(n - j) never below its
+  // value at the smallest reverse position used (xa): when even that sum is above the optimum, no column here is
+  // on an optimal path (the usual case: a corridor is a few columns of the row).
+  const uint32_t ra = (uint32_t)((xb >= 31 ? xb - 31 : 0) & 31);  // xa = that position, in word qa
+  if (bf + bra + (ra ? __popc(wra & ((1u << ra) - 1u)) : 0u) > target) return;
+  const uint32_t brb = pr[qb], wrb = qb < a.w ? vr[qb] : 0u;
   for (uint32_t t = 0; t < 32; ++t) {
     const uint64_t j = j0 + t;
     if (j > a.n) break;
@@ -259,7 +267,8 @@ __device__ uint64_t walk_segment(const TraceArgs& a, uint64_t hi, uint64_t lo, u
 
 // The same walk done by a whole warp (all lanes call it with the same arguments and follow the same path): lane k
 // fetches the words of row i - k at the walk's current 32-column word, so the loads of 32 rows overlap, and the
-// walk takes them from the lanes one row at a time. Lane 0 writes the emitted symbols.
+// walk takes them from the lanes one row at a time; when it moves to another word it fetches again from that row
+// (one round of loads instead of one load per remaining row). Lane 0 writes the emitted symbols.
 __device__ uint64_t walk_segment_warp(const TraceArgs& a, uint64_t hi, uint64_t lo, uint64_t e, uint8_t* out_chars,
                                       uint32_t* out_cnt) {
   const uint32_t lane = threadIdx.x & 31;
@@ -278,6 +287,7 @@ __device__ uint64_t walk_segment_warp(const TraceArgs& a, uint64_t hi, uint64_t 
     uint32_t n_dk = __shfl_sync(kFull, dv, 0), n_pak = __shfl_sync(kFull, pa, 0), n_pbk = __shfl_sync(kFull, pb, 0);
     for (uint32_t k = 0; k < 32; ++k) {
       if (i <= lo || j == 0) break;  // the same on every lane
+      if ((int64_t)(j >> 5) != Qg) break;  // the walk left the fetched word: fetch again from this row, at its word
       const uint32_t code = n_code, sym = n_sym, dk = n_dk, pak = n_pak, pbk = n_pbk;
       const uint32_t kn = (k + 1) & 31;
       n_code = __shfl_sync(kFull, cd, kn);
@@ -336,20 +346,37 @@ __device__ uint64_t walk_segment_warp(const TraceArgs& a, uint64_t hi, uint64_t 
   return j;
 }
 
-// Walker k of segment s (block (s, k / 32), thread k % 32) walks from the k-th corridor column found. The last
-// segment has one walker, from (m, n); it records that entry for the chain pass.
+// Walkers of segment s. A segment whose corridor has at most gridDim.y columns (the usual case for pairs of similar
+// length) gives each walker a whole warp: block (s, k) walks from the k-th corridor column with
+// walk_segment_warp, whose lanes fetch 32 rows at a time and follow one path, so a row costs a few dependent
+// instructions and no divergence. A wider corridor (tall pairs, hundreds of columns) runs one walker per thread:
+// block (s, y), thread t walks from column y * 32 + t. The last segment has one walker, from (m, n); it records
+// that entry for the chain pass.
 __global__ void k_walk(TraceArgs a) {
   const uint64_t s = blockIdx.x;
-  const uint32_t k = blockIdx.y * kWalkers + threadIdx.x;
   const bool last = s + 1 == a.S;
-  const uint32_t cnt = last ? 1u : a.ent_cnt[s];
-  if (k >= (cnt < a.W ? cnt : a.W)) return;
+  const uint32_t found = last ? 1u : a.ent_cnt[s];
+  const uint32_t cnt = found < a.W ? found : a.W;
   const uint64_t lo = s * a.H, hi = (s + 1) * a.H < a.m ? (s + 1) * a.H : a.m;
-  const uint64_t e = last ? a.n : a.ent[s * a.W + k];
-  if (last) {
-    a.ent[s * a.W] = (uint32_t)a.n;
-    a.ent_cnt[s] = 1;
+  if (cnt <= gridDim.y) {  // a warp per walker
+    const uint32_t k = blockIdx.y;
+    if (k >= cnt) return;
+    const uint64_t e = last ? a.n : a.ent[s * a.W + k];
+    uint32_t nc = 0;
+    const uint64_t x = walk_segment_warp(a, hi, lo, e, a.chars + (s * (a.W + 1) + k) * a.H, &nc);
+    if (threadIdx.x == 0) {
+      if (last) {
+        a.ent[s * a.W] = (uint32_t)a.n;
+        a.ent_cnt[s] = 1;
+      }
+      a.ext[s * a.W + k] = (uint32_t)x;
+      a.nch[s * a.W + k] = nc;
+    }
+    return;
   }
+  const uint32_t k = blockIdx.y * kWalkers + threadIdx.x;  // a thread per walker
+  if (k >= cnt) return;
+  const uint64_t e = a.ent[s * a.W + k];
   uint32_t nc = 0;
   const uint64_t x = walk_segment(a, hi, lo, e, a.chars + (s * (a.W + 1) + k) * a.H, &nc);
   a.ext[s * a.W + k] = (uint32_t)x;
@@ -569,7 +596,9 @@ cudaError_t launch_traceback(const TraceArgs& a, cudaStream_t st) {
     const uint64_t gx = (a.n / 32 + 1 + 127) / 128;  // one thread per 32-column word
     k_corr_cols<<<dim3((unsigned)gx, (unsigned)(a.S - 1)), 128, 0, st>>>(a);
   }
-  k_walk<<<dim3((unsigned)a.S, a.W / kWalkers), kWalkers, 0, st>>>(a);
+  // gridDim.y: enough blocks for W walkers of a thread each, and at least kWarpWalkers (a warp per walker)
+  const unsigned walk_y = (unsigned)std::max<uint64_t>(a.W / kWalkers, kWarpWalkers);
+  k_walk<<<dim3((unsigned)a.S, walk_y), kWalkers, 0, st>>>(a);
   const size_t chain_smem = (size_t)(2 * a.S * kWalkers + a.S) * sizeof(uint32_t) + a.S * kWalkers;
   cudaError_t e = once_per_device_attr(
       [] {
