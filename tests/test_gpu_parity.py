@@ -171,3 +171,27 @@ def test_reused_context_after_alphabet_change(ctx, oracle):
         x, y = gen.pair_uniform(1500 + 17 * k, 3000 - 31 * k, sigma, seed=4200 + k)
         assert ctx.length(x, y) == oracle.lcs_length(x, y)
         assert ctx.traceback(x, y) == oracle.lcs_traceback(x, y)
+
+
+# The shapes of the paper's Table 1 (parent length M rows, child length N columns). The tall ones make corridors of
+# hundreds of columns (a thread per walker in the traceback); the square-ish ones make narrow corridors (a warp
+# per walker).
+TABLE1_SHAPES = [(10, 5), (100, 10), (200, 30), (500, 80), (800, 100), (1000, 150), (2000, 200), (5000, 200),
+                 (5000, 400), (5000, 800), (5000, 1000), (10000, 1000), (10000, 1500)]
+
+
+@pytest.mark.parametrize("k", range(len(TABLE1_SHAPES)))
+def test_table1_shapes(ctx, oracle, k):
+    m, n = TABLE1_SHAPES[k]
+    x, y = gen.pair_uniform(m, n, 4, seed=gen.BASE_SEED + 100 + k)
+    check_pair(ctx, oracle, x, y)
+
+
+@pytest.mark.parametrize("m,n", [(20000, 3000), (3000, 20000), (12000, 12000)])
+def test_wide_and_narrow_corridors(ctx, oracle, m, n):
+    """Tall, wide and square pairs of related strings (Y a mutated piece of X, or the other way round)."""
+    base = gen.random_string(77, max(m, n), gen.DNA)
+    longer = base[: max(m, n)]
+    shorter = gen.mutate(longer, seed=78, alphabet=gen.DNA, out_len=min(m, n))
+    x, y = (longer, shorter) if m >= n else (shorter, longer)
+    check_pair(ctx, oracle, x, y)
