@@ -313,6 +313,7 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": traffic, "kernel": "k_fill<8,true>", "peak_source": src,
                      "note": "algorithmic bytes = m*n/8 (1-bit direction bitmap) per launch"},
+        "roofline_alu": alu_line(cells, 6, f_ms, clocks, "k_fill<8,true> (traceback mode)"),
         "cpu_baseline": cpu,
         "cpu_baseline_all_cores": cpu_par,
         "e2e": {"value": ws * cells / e2e_s / 1e9, "unit": "GCUPS", "stat": "median of the timed calls",
@@ -332,6 +333,18 @@ def run_gpu(args):
 def alu_peak_tops(sm_mhz: float, sms: int = 152) -> float:
     """INT32 ALU peak from unit counts and clock: 64 INT32 lanes per SM per clock (LOP3/IADD3) x SMs x clock."""
     return sms * 64 * sm_mhz * 1e6 / 1e12
+
+
+def alu_line(cells: int, ops_per_word: int, kernel_ms: float, clocks: dict, kernel: str) -> dict:
+    """The fill kernel against the INT32 ALU roofline: algorithmic work = ops_per_word INT32 operations per 32 cells
+    (4 for the row update, 6 with the direction bitmap), over the kernel's event-timed duration."""
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    peak = alu_peak_tops(sm_mhz)
+    achieved = cells / 32 * ops_per_word / (kernel_ms * 1e-3) / 1e12
+    return {"bound": "alu (dependency chain in practice)", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+            "frac": achieved / peak, "kernel": kernel, "ops_per_32_cells": ops_per_word,
+            "note": "peak = 152 SMs x 64 INT32/clk x sampled SM clock; the single-pair fill is a wavefront whose "
+                    "serial chain of steps, not the ALU, sets its time"}
 
 
 def run_batch_workload(args):
@@ -470,6 +483,9 @@ def run_long_workload(args):
     ctx.set_profiling(True)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
     for sigma in (4, 20):
         x, y = gen.pair_uniform(262144, 262144, sigma, seed=gen.BASE_SEED + 2)
         dx, dy = torch.from_numpy(x.copy()).to(dev), torch.from_numpy(y.copy()).to(dev)
@@ -490,6 +506,7 @@ def run_long_workload(args):
             ts.append(ev0.elapsed_time(ev1))
             fs.append(p["fill_ms"])
         res[sigma] = (float(np.median(ts)), float(np.median(fs)), int(out.item()))
+    clocks = sampler.stop()
     cells = 262144 ** 2
     t4 = res[4][0]
     line = {
@@ -500,6 +517,10 @@ def run_long_workload(args):
                    "sigma20_gcups": cells / (res[20][0] * 1e-3) / 1e9, "lcs_length": {4: res[4][2], 20: res[20][2]},
                    "l2": "explicit 256 MiB L2 flush before every timed call (outside the events)"},
         "stages_ms": {"fill_sigma4": res[4][1], "fill_sigma20": res[20][1]},
+        "roofline": alu_line(cells, 4, res[4][1], clocks, "k_fill<8,false> (length only, meet in the middle)"),
+        # per call: k_alphabet, k_peq, k_xoff, k_fill, k_combine_pre, k_combine_min, k_combine_fin; both alphabets
+        "gpu_launches": 2 * 7 * args.steps,
+        "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
     ctx.close()
