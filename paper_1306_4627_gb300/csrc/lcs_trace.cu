@@ -4,8 +4,9 @@
 // else LEFT. At row i the walk moves left past LEFT cells to the first column c <= j that is a match or an UP
 // cell, then steps to row i-1 (to column c-1 on a match, to c otherwise). That is one word scan per row here.
 //
-// The rows are cut into S segments of H rows; every segment is walked at once by a warp of up to 32 walkers.
-// Where the true path enters a segment is unknown until the segment below is done, but it must lie on an optimal
+// The rows are cut into S segments of H rows, and every segment is walked at once by its walkers (a warp each when
+// the segment has at most 32 of them, a thread each otherwise). Where the true path enters a segment is unknown
+// until the segment below is done, but it must lie on an optimal
 // path, so it is one of the columns j of the segment's bottom row with c[i,j] + LCS(X[i+1..m], Y[j+1..n]) = c[m,n]
 // ("corridor" columns). The prefix lengths c[i,.] come from V snapshots of the forward fill, the suffix lengths
 // from V snapshots of the same fill run on the reversed strings. Every corridor column gets a walker; a short
