@@ -756,6 +756,51 @@ static cudaError_t batch_launches(lcs_ctx* c, uint64_t* d_out, uint64_t count, c
   return e;
 }
 
+// Uploads the plan's parts to c->bplan at their byte offsets: packed into the context's pinned plan buffer and sent
+// with one asynchronous copy (the previous upload from that buffer is waited for before it is overwritten), or,
+// when no pinned buffer can be had, with one copy per part from the host vectors (the runtime stages those).
+static int upload_plan(lcs_ctx* c, const Plan& plan, size_t jat, size_t iat, size_t sat, size_t oat,
+                       cudaStream_t st) {
+  const size_t pb = plan.pairs.size() * sizeof(BPair), jb = plan.jobs.size() * sizeof(BJob),
+               ib = plan.items.size() * sizeof(BItem), sb = plan.split.size() * 4, ob = plan.prep_order.size() * 4;
+  const size_t total = oat + ob;
+  char* base = (char*)c->bplan.p;
+  bool pinned = true;
+  if (c->hplan_ev) pinned = cudaEventSynchronize(c->hplan_ev) == cudaSuccess;  // the last upload has left hplan
+  if (pinned && !c->hplan_ev) pinned = cudaEventCreateWithFlags(&c->hplan_ev, cudaEventDisableTiming) == cudaSuccess;
+  if (pinned && total > c->hplan_cap) {
+    if (c->hplan) cudaFreeHost(c->hplan);
+    c->hplan = nullptr;
+    c->hplan_cap = 0;
+    void* p = nullptr;
+    const size_t want = std::max<size_t>(total + total / 4, 1 << 16);
+    if (cudaMallocHost(&p, want) == cudaSuccess) {
+      c->hplan = static_cast<uint8_t*>(p);
+      c->hplan_cap = want;
+    } else {
+      cudaGetLastError();  // clear the failed allocation; fall back to pageable copies
+      pinned = false;
+    }
+  }
+  if (pinned) {
+    std::memcpy(c->hplan, plan.pairs.data(), pb);
+    std::memcpy(c->hplan + jat, plan.jobs.data(), jb);
+    std::memcpy(c->hplan + iat, plan.items.data(), ib);
+    if (sb) std::memcpy(c->hplan + sat, plan.split.data(), sb);
+    std::memcpy(c->hplan + oat, plan.prep_order.data(), ob);
+    int rc = from_cuda(cudaMemcpyAsync(base, c->hplan, total, cudaMemcpyHostToDevice, st));
+    if (!rc) rc = from_cuda(cudaEventRecord(c->hplan_ev, st));
+    return rc;
+  }
+  // (copies from pageable memory: the runtime has staged the data when the call returns)
+  int rc = from_cuda(cudaMemcpyAsync(base, plan.pairs.data(), pb, cudaMemcpyHostToDevice, st));
+  if (!rc) rc = from_cuda(cudaMemcpyAsync(base + jat, plan.jobs.data(), jb, cudaMemcpyHostToDevice, st));
+  if (!rc) rc = from_cuda(cudaMemcpyAsync(base + iat, plan.items.data(), ib, cudaMemcpyHostToDevice, st));
+  if (!rc && sb) rc = from_cuda(cudaMemcpyAsync(base + sat, plan.split.data(), sb, cudaMemcpyHostToDevice, st));
+  if (!rc) rc = from_cuda(cudaMemcpyAsync(base + oat, plan.prep_order.data(), ob, cudaMemcpyHostToDevice, st));
+  return rc;
+}
+
 // Runs a batch whose xs / ys / out_lens are already on the device. The first call of a batch plans it on the host,
 // uploads the plan and launches; a later call with the same pairs (same offsets and buffers) reuses the plan, and
 // without profiling its launches are captured once as a CUDA graph and replayed.
@@ -793,13 +838,7 @@ int run_batch(lcs_ctx* c, const uint8_t* d_xs, const uint8_t* d_ys, const uint64
       if (!rc) rc = from_cuda(ensure(c->bpeq, plan.peq_words * 4 + 4));
       if (!rc) rc = from_cuda(ensure(c->bfv, ((uint64_t)plan.fv_slots * kRowWords + 4) * 4));
       if (rc) return rc;
-      // (copies from pageable memory: the runtime has staged the data when the call returns)
-      char* base = (char*)c->bplan.p;
-      rc = from_cuda(cudaMemcpyAsync(base, plan.pairs.data(), pb, cudaMemcpyHostToDevice, st));
-      if (!rc) rc = from_cuda(cudaMemcpyAsync(base + jat, plan.jobs.data(), jb, cudaMemcpyHostToDevice, st));
-      if (!rc) rc = from_cuda(cudaMemcpyAsync(base + iat, plan.items.data(), ib, cudaMemcpyHostToDevice, st));
-      if (!rc && sb) rc = from_cuda(cudaMemcpyAsync(base + sat, plan.split.data(), sb, cudaMemcpyHostToDevice, st));
-      if (!rc) rc = from_cuda(cudaMemcpyAsync(base + oat, plan.prep_order.data(), ob, cudaMemcpyHostToDevice, st));
+      rc = upload_plan(c, plan, jat, iat, sat, oat, st);
       if (rc) return rc;
     }
     c->bnpairs = plan.pairs.size();

@@ -67,6 +67,10 @@ struct lcs_ctx {
   uint64_t* host_tail = nullptr;  // 8 words
   uint8_t* hstage = nullptr;
   size_t hstage_cap = 0;
+  // pinned copy of the last batch plan (uploaded with one asynchronous copy; the event marks that copy's end)
+  uint8_t* hplan = nullptr;
+  size_t hplan_cap = 0;
+  cudaEvent_t hplan_ev = nullptr;
   // stage events of the last profiled call: [0] start, [1] fill start, [2] fill end, [3] end
   bool prof = false, prof_valid = false, prof_trace = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -86,6 +90,12 @@ struct lcs_ctx {
     if (hstage) cudaFreeHost(hstage);
     hstage = nullptr;
     hstage_cap = 0;
+    if (hplan_ev) cudaEventSynchronize(hplan_ev);
+    if (hplan) cudaFreeHost(hplan);
+    hplan = nullptr;
+    hplan_cap = 0;
+    if (hplan_ev) cudaEventDestroy(hplan_ev);
+    hplan_ev = nullptr;
     if (bexec) cudaGraphExecDestroy(bexec);
     bexec = nullptr;
     bvalid = false;
