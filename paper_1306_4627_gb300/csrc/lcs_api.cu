@@ -142,9 +142,25 @@ static int prep_y(lcs_ctx* c, const uint8_t* d_y, uint64_t n, const Geo& g, bool
   return rc;
 }
 
+// A small pair in one launch (lcs_small.cu): its stages are all under the fill's marks.
+static int run_small(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, uint64_t n, bool traceback,
+                     uint8_t* d_out, uint64_t out_cap, uint64_t* d_out_len, cudaStream_t st) {
+  c->mark(0, st);
+  c->mark(1, st);
+  const int rc = from_cuda(launch_small(d_x, m, d_y, n, traceback, d_out, out_cap, d_out_len, c->status(), st));
+  c->mark(2, st);
+  c->mark(3, st);
+  c->prof_valid = c->prof;
+  c->prof_trace = traceback;
+  c->prof_blocks = 1;
+  c->prof_cells = m * n;
+  return rc;
+}
+
 int run_length(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, uint64_t n, uint64_t* d_out,
                cudaStream_t st) {
   if (m == 0 || n == 0) return from_cuda(cudaMemsetAsync(d_out, 0, sizeof(uint64_t), st));
+  if (c->small_path && small_pair(m, n)) return run_small(c, d_x, m, d_y, n, false, nullptr, 0, d_out, st);
   const uint32_t B = c->fill_B;
   const Geo g = geo_for(n);
   // Meet in the middle: the top half of the rows forward, the bottom half on the reversed strings, at the same
@@ -213,6 +229,7 @@ int run_length(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, u
 int run_traceback(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, uint64_t n, uint8_t* d_out,
                   uint64_t out_cap, uint64_t* d_out_len, cudaStream_t st) {
   if (m == 0 || n == 0) return from_cuda(cudaMemsetAsync(d_out_len, 0, sizeof(uint64_t), st));
+  if (c->small_path && small_pair(m, n)) return run_small(c, d_x, m, d_y, n, true, d_out, out_cap, d_out_len, st);
   const uint32_t B = c->fill_B_tb;
   const Geo g = geo_for(n);
   // Segments of H rows for the parallel walk, at most kMaxSegments of them. H is a multiple of 32 * B: the fill
@@ -400,6 +417,8 @@ extern "C" int lcs_ctx_create(int device, lcs_ctx** out) {
   if (const char* e = getenv("LCS_SPIN_LIMIT")) c->spin_limit = (uint32_t)std::max(64, atoi(e));
   if (const char* e = getenv("LCS_DEBUG_DROP_HANDOFF")) c->debug_drop = atoi(e) ? 1u : 0u;
   if (const char* e = getenv("LCS_BATCH_BLOCKS_PER_SM")) c->batch_blocks_per_sm = atoi(e);
+  // test hook: small pairs through the general path too
+  if (const char* e = getenv("LCS_NO_SMALL_PATH")) c->small_path = atoi(e) == 0;
   *out = c;
   return LCS_OK;
 }

@@ -48,6 +48,7 @@ struct lcs_ctx {
   int batch_blocks_per_sm = 0;
   uint32_t bk_max = 4;  // the planned batch's largest words per lane
   uint32_t debug_drop = 0;    // test hook (environment LCS_DEBUG_DROP_HANDOFF): a hand-off that never comes
+  bool small_path = true;     // small pairs in one launch (lcs_small.cu); environment LCS_NO_SMALL_PATH=1 turns it off
   std::mutex mu;
   lcs::DBuf small, x, y, out;
   lcs::DBuf xoff_f, xoff_r, xcode, peq_f, peq_r, carry_f, carry_r, fv_f, fv_r, T, snap_f, snap_r;

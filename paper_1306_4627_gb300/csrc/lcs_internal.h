@@ -146,5 +146,11 @@ cudaError_t launch_traceback(const TraceArgs& t, cudaStream_t st);
 cudaError_t launch_tables(const TraceArgs& t, const uint8_t* y, uint32_t* sums, uint32_t* c, uint8_t* b,
                           cudaStream_t st);
 uint64_t tables_sum_words(uint64_t m, uint64_t n);
+// small pairs in one launch (one warp, masks and bitmap in shared memory): length, and the LCS in traceback mode
+constexpr uint64_t kSmallMaxRows = 1024;
+constexpr uint64_t kSmallMaxCols = 992;  // 31 words, so the row's words and the column-n carry fit one warp
+bool small_pair(uint64_t m, uint64_t n);
+cudaError_t launch_small(const uint8_t* x, uint64_t m, const uint8_t* y, uint64_t n, bool traceback, uint8_t* out,
+                         uint64_t out_cap, uint64_t* out_len, DevStatus* status, cudaStream_t st);
 
 }  // namespace lcs

@@ -195,3 +195,37 @@ def test_wide_and_narrow_corridors(ctx, oracle, m, n):
     shorter = gen.mutate(longer, seed=78, alphabet=gen.DNA, out_len=min(m, n))
     x, y = (longer, shorter) if m >= n else (shorter, longer)
     check_pair(ctx, oracle, x, y)
+
+
+# ---- small pairs: the one-launch path and the general path --------------------------------------------------------
+@pytest.fixture(scope="module")
+def ctx_general():
+    """A context whose small pairs take the general (multi-kernel) path as well (test hook LCS_NO_SMALL_PATH)."""
+    from paper_1306_4627_gb300 import lcs
+    os.environ["LCS_NO_SMALL_PATH"] = "1"
+    try:
+        c = lcs.Context(0)
+    finally:
+        del os.environ["LCS_NO_SMALL_PATH"]
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("m", [1, 9, 33, 1023, 1024, 1025])
+@pytest.mark.parametrize("n", [1, 31, 32, 33, 991, 992, 993])
+def test_small_shapes_both_paths(ctx, ctx_general, oracle, m, n):
+    """Around the limits of the one-launch path (m <= 1024, n <= 992; 992 = 31 words, so the carry for column n
+    has its own word), on both paths."""
+    x, y = gen.pair_uniform(m, n, 4, seed=5000 + 7 * m + n)
+    check_pair(ctx, oracle, x, y)
+    check_pair(ctx_general, oracle, x, y)
+
+
+@pytest.mark.parametrize("sigma", [2, 20, 256])
+def test_small_path_alphabets_and_related(ctx, ctx_general, oracle, sigma):
+    alpha = {2: b"AB", 20: gen.PROTEIN, 256: gen.BYTES}[sigma]
+    x = gen.random_string(6000 + sigma, 700, alpha)
+    y = gen.mutate(x, seed=6001 + sigma, alphabet=alpha, out_len=640)
+    for c in (ctx, ctx_general):
+        check_pair(c, oracle, x, y)
+        check_pair(c, oracle, y, x)
