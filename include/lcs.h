@@ -140,7 +140,8 @@ LCS_API int lcs_length_noalloc(const uint8_t* d_x, uint64_t m, const uint8_t* d_
 /* Host buffers. Writes the LCS (forward order) to out[0..len) and len to *out_len. out_cap >= min(m, n) is always
  * enough; a smaller out_cap that cannot hold the result gives LCS_ERR_CAPACITY with *out_len = the LCS length.
  * Device memory of about m*n/8 bytes (a 1-bit-per-cell direction bitmap) is needed: LCS_ERR_NOMEM when it
- * cannot be allocated. Blocking. */
+ * cannot be allocated. Blocking. (Pairs with m <= 1024 and n <= 992, for lcs_length* as well, run as one launch
+ * with the bitmap in on-chip memory; the results are the same.) */
 LCS_API int lcs_traceback(lcs_ctx* ctx, const uint8_t* x, uint64_t m, const uint8_t* y, uint64_t n, uint8_t* out,
                   uint64_t out_cap, uint64_t* out_len);
 
