@@ -87,3 +87,17 @@ def test_partition_balances_cells():
         # greedy largest-first: no shard exceeds another by more than the largest pair
         assert max(loads) - min(loads) <= int((m * n).max())
     assert [p.tolist() for p in shard.partition_pairs([3, 1, 2], [1, 1, 1], 2)] == [[0], [1, 2]]
+
+
+def test_partition_edge_cases():
+    from paper_1306_4627_gb300 import shard
+    assert [len(p) for p in shard.partition_pairs([], [], 3)] == [0, 0, 0]
+    parts = shard.partition_pairs([5], [7], 4)  # more ranks than pairs: one rank works, the others get nothing
+    assert [len(p) for p in parts] == [1, 0, 0, 0] and shard.shard_cells([5], [7], parts) == [35, 0, 0, 0]
+    parts = shard.partition_pairs([0, 3, 0, 9], [4, 0, 0, 9], 2)  # empty pairs (no cells) are still assigned
+    assert sorted(int(k) for p in parts for k in p) == [0, 1, 2, 3]
+    import pytest
+    with pytest.raises(ValueError):
+        shard.partition_pairs([1, 2], [3], 2)
+    with pytest.raises(ValueError):
+        shard.partition_pairs([1], [1], 0)
