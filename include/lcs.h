@@ -106,6 +106,38 @@ LCS_API int lcs_ctx_set_fill_config(lcs_ctx* ctx, uint32_t mode, const lcs_fill_
 LCS_API int lcs_ctx_autotune_dev(lcs_ctx* ctx, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, uint64_t n,
                                  uint32_t mode, void* stream, lcs_fill_config* best, double* best_ms);
 
+/* ---- measurement probes (no counterpart in the paper: the ceilings the table fill is measured against) --------- */
+
+/* INT32 throughput of the whole device for one instruction sequence, every SM full of independent chains.
+ * mix 0: the row update of one 32-column word of the §I.C recurrence in bit-parallel form (U = V & P; the carry-in
+ *        shift, S = V + U + carry and the carry collection; V' = S | (V & ~P)): 5 instructions;
+ * mix 1: the same plus the traceback's direction word T = S ^ V ^ U: 6 instructions;
+ * mix 2: one three-input logic operation.
+ * iters: loop iterations per thread (each runs 4 chains); 200000 takes some tens of milliseconds. */
+typedef struct lcs_int_rate {
+  double ops_per_s;        /* instructions of the mix per second over the device (CUDA-event timed launch) */
+  double ops_per_clk_sm;   /* per SM and SM clock cycle (cycles from clock64 in every block, the longest) */
+  double sm_clock_mhz;     /* SM clock during the launch: cycles / event time */
+  double kernel_ms;        /* event time of the timed launch */
+  int32_t sms;             /* multiprocessors of the device (cudaDevAttrMultiProcessorCount) */
+  int32_t blocks_per_sm;   /* resident blocks of 256 threads per SM */
+  uint32_t ops_per_chain;  /* instructions per chain and iteration of the mix (5, 6 or 1) */
+  uint32_t threads;        /* threads of the launch */
+} lcs_int_rate;
+
+/* Runs two launches on `device` (a warm-up, then the timed one) with buffers it allocates and frees. Blocking.
+ * Errors: LCS_ERR_INVALID (out NULL, mix > 2, iters 0, no such device), LCS_ERR_CUDA. */
+LCS_API int lcs_probe_int_rate(int device, uint32_t mix, uint32_t iters, lcs_int_rate* out);
+
+/* The dependency floor of one systolic step of the table fill: clock cycles per step of rows_per_step (8 or 16)
+ * rows when one warp per SM sub-partition runs only the fill's row arithmetic and its two carry shuffles per step
+ * (match masks in registers; in traceback mode (traceback != 0) also the fill's two 16-byte bitmap stores per lane).
+ * steps (1 .. 2^24) are timed with clock64 after 64 untimed ones; *cycles_per_step is the median of the 4 warps.
+ * Multiplied by the fill's chain of steps (row-blocks + one step per 32-column word of the row) it bounds the time
+ * of one pair's fill from below. Blocking. Errors: LCS_ERR_INVALID, LCS_ERR_CUDA. */
+LCS_API int lcs_probe_step_floor(int device, uint32_t rows_per_step, int traceback, uint32_t steps,
+                                 double* cycles_per_step);
+
 /* ---- length (paper §I.C, LCS-length; returns c[m,n]) --------------------------------------------------------- */
 
 /* Host buffers x[0..m), y[0..n); writes c[m,n] to *out_len. Blocking. m = 0 or n = 0 gives 0. Errors:
@@ -130,8 +162,11 @@ LCS_API int lcs_length_dev(lcs_ctx* ctx, const uint8_t* d_x, uint64_t m, const u
  *     start at zero). Calls that overlapped on the GPU would race on it; this entry point therefore serialises its
  *     calls per device and waits for each one.
  *   - d_x, d_y and d_out_len are device pointers owned by the caller. The work is enqueued on `stream` (NULL = the
- *     default stream); the call returns after the stream has finished it, with c[m,n] in *d_out_len on LCS_OK.
- *   - Errors: LCS_ERR_INVALID, LCS_ERR_CUDA, LCS_ERR_TIMEOUT. */
+ *     default stream); the call returns after the stream has finished it, with c[m,n] in *d_out_len on LCS_OK. It
+ *     also waits for its own work when it fails part way, so a failed call leaves nothing running on the array.
+ *   - The call never falls back to allocating: the per-call buffers are fixed parts of the array, and a request that
+ *     did not fit one of them fails with LCS_ERR_INTERNAL.
+ *   - Errors: LCS_ERR_INVALID, LCS_ERR_CUDA, LCS_ERR_TIMEOUT, LCS_ERR_INTERNAL. */
 LCS_API int lcs_length_noalloc(const uint8_t* d_x, uint64_t m, const uint8_t* d_y, uint64_t n, uint64_t* d_out_len,
                                void* stream);
 

@@ -36,6 +36,10 @@ int from_cuda(cudaError_t e) {
 
 cudaError_t ensure(DBuf& b, size_t bytes) {
   if (bytes <= b.cap) return cudaSuccess;
+  if (b.fixed) {  // neither freed nor replaced: the caller sees an allocation failure and the flag tells why
+    b.overflow = true;
+    return cudaErrorMemoryAllocation;
+  }
   if (b.p) {
     cudaError_t e = cudaFree(b.p);
     b.p = nullptr;
@@ -55,6 +59,7 @@ cudaError_t ensure(DBuf& b, size_t bytes) {
 }
 
 void release(DBuf& b) {
+  if (b.fixed) return;
   if (b.p) cudaFree(b.p);
   b.p = nullptr;
   b.cap = 0;

@@ -12,6 +12,8 @@ namespace lcs {
 struct DBuf {
   void* p = nullptr;
   size_t cap = 0;
+  bool fixed = false;     // memory the buffer does not own (a carved part of a static array): never freed or grown
+  bool overflow = false;  // set when a request did not fit a fixed buffer (ensure() then fails instead of growing)
 };
 
 cudaError_t ensure(DBuf& b, size_t bytes);

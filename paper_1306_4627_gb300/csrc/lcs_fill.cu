@@ -20,6 +20,8 @@
 //   * all blocks are co-resident (cooperative launch), one block of 4 warps per SM;
 //   * every wait is bounded: when it expires the kernel records a timeout in the status word and runs to the end
 //     without waiting, so the host gets LCS_ERR_TIMEOUT instead of a hung GPU.
+#include <algorithm>
+
 #include "lcs_internal.h"
 
 namespace lcs {
@@ -523,6 +525,80 @@ cudaError_t launch_t(const FillArgs& a, cudaStream_t st) {
   return cudaLaunchCooperativeKernel((const void*)fn, dim3(grid), dim3(kFillThreads), args, smem, st);
 }
 
+// ---- step floor probe --------------------------------------------------------------------------------------------
+// The fill's step without the work around it: one block of 4 warps (one per SM sub-partition, as in the fill) runs
+// `steps` systolic steps of B rows with exactly the fill's row arithmetic (rows<B, TB>: the row updates and the two
+// carry shuffles per step), the match masks held in registers, and in traceback mode the fill's two 16-byte bitmap
+// stores per lane and step (into a 64-step ring per warp that stays in L2). Each warp times its steps with clock64
+// after 64 untimed ones. Index ranges: masks[0..64), cycles[0..4), sink[0..128),
+// tbuf[0 .. 4 warps * 64 slots * 32 lanes * B words) with B <= 16.
+template <int B, bool TB>
+__global__ void __launch_bounds__(kFillThreads, 1)
+    k_step_floor(const uint32_t* masks, uint32_t steps, unsigned long long* cycles, uint32_t* sink, uint4* tbuf) {
+  const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  uint32_t P[B];
+#pragma unroll
+  for (int b = 0; b < B; ++b) P[b] = masks[(threadIdx.x * B + b) & 63];
+  uint32_t V = kFull, cin_a = 0, cin_b = 0, acc = 0;
+  uint4* tp = tbuf + (size_t)wib * 64 * 32 * (B / 4) + lane;  // the fill's chunk layout: [B/4][32 lanes] vectors
+  long long t0 = 0;
+#pragma unroll 1
+  for (uint32_t t = 0; t < steps + 64; ++t) {
+    if (t == 64) t0 = clock64();
+    uint32_t co, tw[B];
+    rows<B, TB>(P, V, cin_a, cin_b, co, cin_a, cin_b, tw);
+    acc += co;
+    if (TB) {
+      uint4* q = tp + (size_t)(t & 63) * 32 * (B / 4);
+#pragma unroll
+      for (int v = 0; v < B / 4; ++v) q[v * 32] = make_uint4(tw[4 * v], tw[4 * v + 1], tw[4 * v + 2], tw[4 * v + 3]);
+    }
+  }
+  const long long t1 = clock64();
+  if (lane == 0) cycles[wib] = (unsigned long long)(t1 - t0);
+  sink[threadIdx.x] = V ^ acc;
+}
+
+template <int B, bool TB>
+cudaError_t step_floor_t(uint32_t steps, double* cycles_per_step) {
+  uint32_t *masks = nullptr, *sink = nullptr;
+  unsigned long long* cyc = nullptr;
+  uint4* tbuf = nullptr;
+  const size_t tbuf_bytes = (size_t)4 * 64 * 32 * 16 * 4;
+  cudaError_t e = cudaMalloc(&masks, 64 * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&sink, kFillThreads * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&cyc, kFillWarps * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&tbuf, tbuf_bytes);
+  if (e == cudaSuccess) {
+    uint32_t h[64];
+    uint64_t z = 0x9E3779B97F4A7C15ull;
+    for (int k = 0; k < 64; ++k) {  // fixed pseudo-random masks (splitmix64 outputs)
+      z += 0x9E3779B97F4A7C15ull;
+      uint64_t v = z;
+      v = (v ^ (v >> 30)) * 0xBF58476D1CE4E5B9ull;
+      v = (v ^ (v >> 27)) * 0x94D049BB133111EBull;
+      h[k] = (uint32_t)(v ^ (v >> 31));
+    }
+    e = cudaMemcpy(masks, h, sizeof(h), cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) {
+    k_step_floor<B, TB><<<1, kFillThreads>>>(masks, steps, cyc, sink, tbuf);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  unsigned long long hc[kFillWarps] = {0, 0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpy(hc, cyc, sizeof(hc), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) {
+    std::sort(hc, hc + kFillWarps);
+    *cycles_per_step = 0.5 * (double)(hc[1] + hc[2]) / (double)steps;  // median of the 4 warps
+  }
+  cudaFree(masks);
+  cudaFree(sink);
+  cudaFree(cyc);
+  cudaFree(tbuf);
+  return e;
+}
+
 }  // namespace
 
 size_t fill_smem_bytes() {
@@ -553,6 +629,12 @@ cudaError_t launch_b(const FillArgs& a, bool traceback, cudaStream_t st) {
 cudaError_t launch_fill(const FillArgs& a, uint32_t B, bool traceback, cudaStream_t st) {
   if (B == 8) return launch_b<8, 16, 32>(a, traceback, st);
   if (B == 16) return launch_b<16, 8, 16>(a, traceback, st);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t step_floor(uint32_t B, bool traceback, uint32_t steps, double* cycles_per_step) {
+  if (B == 8) return traceback ? step_floor_t<8, true>(steps, cycles_per_step) : step_floor_t<8, false>(steps, cycles_per_step);
+  if (B == 16) return traceback ? step_floor_t<16, true>(steps, cycles_per_step) : step_floor_t<16, false>(steps, cycles_per_step);
   return cudaErrorInvalidValue;
 }
 

@@ -7,9 +7,12 @@
 // cudaGetSymbolAddress while that device is current, and carves the per-call buffers out of it. Every call on a
 // device shares the array and leaves its contents behind; the length path clears everything that must start at
 // zero (carry slots, length accumulator) before each use, and the status word is cleared whenever it reports an
-// error. Calls are serialised per device on the host and each call waits for its own work, so two calls of this
-// entry point never overlap on the GPU; work that the caller enqueues on other streams while a call runs must not
-// touch the array (nothing outside this file can).
+// error. Calls are serialised per device on the host and each call waits for its own work (also when it fails after
+// enqueueing part of it), so two calls of this entry point never overlap on the GPU; work that the caller enqueues
+// on other streams while a call runs must not touch the array (nothing outside this file can).
+//
+// The carved buffers are marked fixed: the length path's grow-only ensure() never frees or replaces them. A request
+// that did not fit one (a sizing mistake in carve()) fails the call with LCS_ERR_INTERNAL instead of allocating.
 #include <mutex>
 #include <functional>
 #include <new>
@@ -19,7 +22,6 @@
 namespace lcs {
 int run_length(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, uint64_t n, uint64_t* d_out,
                cudaStream_t st);
-int take_status(lcs_ctx* c);
 }  // namespace lcs
 
 namespace {
@@ -65,9 +67,35 @@ int carve(lcs_ctx* c, unsigned char* base) {
     if (off + sz > kScratchBytes) return LCS_ERR_INTERNAL;
     p.b->p = base + off;
     p.b->cap = sz;
+    p.b->fixed = true;
     off += sz;
   }
   return LCS_OK;
+}
+
+// True when a request did not fit one of the carved buffers during the last call (clears the flags).
+bool carved_overflow(lcs_ctx* c) {
+  lcs::DBuf* all[] = {&c->small, &c->peq_f, &c->peq_r, &c->xoff_f, &c->xoff_r,
+                      &c->carry_f, &c->carry_r, &c->fv_f, &c->fv_r, &c->colsum};
+  bool any = false;
+  for (lcs::DBuf* b : all) {
+    any = any || b->overflow;
+    b->overflow = false;
+  }
+  return any;
+}
+
+// Reads the status word on the call's own stream (one copy into host stack memory, one wait for that stream) and
+// clears it when it holds an error.
+int status_on_stream(lcs_ctx* c, cudaStream_t st) {
+  lcs::DevStatus h{};
+  int rc = lcs::from_cuda(cudaMemcpyAsync(&h, c->status(), sizeof(h), cudaMemcpyDeviceToHost, st));
+  if (!rc) rc = lcs::from_cuda(cudaStreamSynchronize(st));
+  if (rc) return rc;
+  if (h.flags == 0) return LCS_OK;
+  cudaMemsetAsync(c->status(), 0, sizeof(lcs::DevStatus), st);
+  cudaStreamSynchronize(st);
+  return (h.flags & lcs::kStatTimeout) ? LCS_ERR_TIMEOUT : LCS_ERR_INTERNAL;
 }
 
 void setup(DeviceSlot& slot, int device) {
@@ -116,8 +144,11 @@ extern "C" int lcs_length_noalloc(const uint8_t* d_x, uint64_t m, const uint8_t*
   std::lock_guard<std::mutex> g(slot.mu);
   cudaStream_t st = (cudaStream_t)stream;
   int rc = lcs::run_length(slot.ctx, d_x, m, d_y, n, d_out_len, st);
-  if (rc) return rc;
-  rc = lcs::from_cuda(cudaStreamSynchronize(st));
-  if (rc) return rc;
-  return lcs::take_status(slot.ctx);
+  if (rc) {
+    // part of the call may be enqueued already: let it finish before the next call can use the array
+    cudaStreamSynchronize(st);
+    cudaGetLastError();
+    return carved_overflow(slot.ctx) ? LCS_ERR_INTERNAL : rc;
+  }
+  return status_on_stream(slot.ctx, st);
 }

@@ -26,6 +26,7 @@ EXPORTS = (
     "lcs_serve_poll", "lcs_serve_wait", "lcs_result_release", "lcs_serve_destroy", "lcs_ctx_set_profiling",
     "lcs_ctx_last_profile", "lcs_tables", "lcs_tables_dev", "lcs_ctx_get_fill_config", "lcs_ctx_set_fill_config",
     "lcs_ctx_autotune_dev", "lcs_ctx_get_batch_config", "lcs_ctx_set_batch_config", "lcs_ctx_autotune_batch_dev",
+    "lcs_probe_int_rate", "lcs_probe_step_floor",
 )
 
 
@@ -52,6 +53,12 @@ class FillConfig(ctypes.Structure):
 class BatchConfig(ctypes.Structure):
     _fields_ = [("words_per_lane", ctypes.c_uint32), ("split_pct", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32)]
+
+
+class IntRate(ctypes.Structure):
+    _fields_ = [("ops_per_s", ctypes.c_double), ("ops_per_clk_sm", ctypes.c_double), ("sm_clock_mhz", ctypes.c_double),
+                ("kernel_ms", ctypes.c_double), ("sms", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("ops_per_chain", ctypes.c_uint32), ("threads", ctypes.c_uint32)]
 
 
 class Result(ctypes.Structure):
@@ -95,6 +102,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lcs_ctx_set_batch_config": (ctypes.c_int, [vp, ctypes.POINTER(BatchConfig)]),
         "lcs_ctx_autotune_batch_dev": (ctypes.c_int, [vp, vp, vp, vp, vp, u64, vp, vp, ctypes.POINTER(BatchConfig),
                                                        ctypes.POINTER(ctypes.c_double)]),
+        "lcs_probe_int_rate": (ctypes.c_int, [ctypes.c_int, u32, u32, ctypes.POINTER(IntRate)]),
+        "lcs_probe_step_floor": (ctypes.c_int, [ctypes.c_int, u32, ctypes.c_int, u32, ctypes.POINTER(ctypes.c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -119,6 +128,22 @@ def _u8(a) -> np.ndarray:
     if isinstance(a, (bytes, bytearray, memoryview)):
         return np.frombuffer(bytes(a), dtype=np.uint8)
     return np.ascontiguousarray(a, dtype=np.uint8)
+
+
+def probe_int_rate(device: int = 0, mix: int = 0, iters: int = 200000) -> dict:
+    """INT32 throughput of the device for an instruction mix (0: the row update, 1: with the traceback word,
+    2: three-input logic), see lcs_probe_int_rate."""
+    r = IntRate()
+    _check(_lib.lcs_probe_int_rate(device, mix, iters, ctypes.byref(r)), "lcs_probe_int_rate")
+    return {k: getattr(r, k) for k, _ in IntRate._fields_}
+
+
+def probe_step_floor(device: int = 0, rows_per_step: int = 8, traceback: bool = False, steps: int = 4096) -> float:
+    """Clock cycles of one fill step's row arithmetic and carry shuffles alone (lcs_probe_step_floor)."""
+    c = ctypes.c_double(0.0)
+    _check(_lib.lcs_probe_step_floor(device, rows_per_step, 1 if traceback else 0, steps, ctypes.byref(c)),
+           "lcs_probe_step_floor")
+    return c.value
 
 
 def _p8(a: np.ndarray):

@@ -20,34 +20,51 @@ def ctx():
     c.close()
 
 
-def make_requests(count, seed, max_len=20000):
+def make_requests(count, seed, lo=32, hi=65536, tb_max=16384):
+    """Requests shaped like the serving workload: m and n log-uniform in [lo, hi], alphabet 4, 20 or 256 with equal
+    probability, a quarter of them with traceback (tracebacks drawn with both sides <= tb_max so that the oracle's
+    full b table stays small)."""
     rng = random.Random(seed)
     reqs = []
     for k in range(count):
         sigma = rng.choice([4, 20, 256])
-        m = int(np.exp(rng.uniform(np.log(1), np.log(max_len))))
-        n = int(np.exp(rng.uniform(np.log(1), np.log(max_len))))
+        tb = rng.random() < 0.25
+        top = min(hi, tb_max) if tb else hi
+        m = int(np.exp(rng.uniform(np.log(lo), np.log(top))))
+        n = int(np.exp(rng.uniform(np.log(lo), np.log(top))))
         x, y = gen.pair_uniform(m, n, sigma, seed=10_000 + 7 * k + seed)
-        reqs.append((x, y, rng.random() < 0.25))
+        reqs.append((x, y, tb))
     return reqs
 
 
-def test_mix_equals_alone(ctx, oracle):
+def oracle_answer(oracle, x, y, tb):
+    threads = min(16, os.cpu_count() or 1)
+    if tb:
+        s = oracle.lcs_traceback_par(x, y, threads) if len(x) * len(y) > 1 << 22 else oracle.lcs_traceback(x, y)
+        return len(s), s
+    L = oracle.lcs_length_par(x, y, threads) if len(x) * len(y) > 1 << 22 else oracle.lcs_length(x, y)
+    return L, None
+
+
+def test_mix_equals_alone_and_oracle(ctx, oracle):
+    """Every request of a mixed stream (short and long pairs, all three alphabets, tracebacks of every alphabet)
+    gives the oracle's length, and its string when a traceback was asked for, both in the mix and run alone."""
     from paper_1306_4627_gb300 import lcs
     reqs = make_requests(240, seed=1)
+    assert any(tb and len(set(x.tolist())) > 20 for x, _, tb in reqs)  # a traceback over the 256-symbol alphabet
     srv = lcs.Server(ctx, max_batch=64)
     tickets = [srv.submit(x, y, traceback=tb) for x, y, tb in reqs]
     results = [srv.wait(t, timeout_s=120.0) for t in tickets]
     srv.close()
     for (x, y, tb), r in zip(reqs, results):
+        L, s = oracle_answer(oracle, x, y, tb)
         assert r is not None and r["status"] == 0
-        assert r["length"] == ctx.length(x, y)
+        assert r["length"] == L, (len(x), len(y))
+        assert ctx.length(x, y) == L
         if tb:
-            assert r["lcs"] == ctx.traceback(x, y)
+            assert r["lcs"] == s, (len(x), len(y))
+            assert ctx.traceback(x, y) == s
         assert r["latency_s"] > 0
-    # and a sample against the oracle
-    for (x, y, tb), r in list(zip(reqs, results))[:40]:
-        assert r["length"] == oracle.lcs_length(x, y)
 
 
 def test_poll_and_release(ctx):

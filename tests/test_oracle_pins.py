@@ -145,6 +145,31 @@ def test_runs_closed_form(oracle):
         assert oracle.lcs_length(x, y) == max(min(p, s), min(q, r))
 
 
+def runs_lcs_string(p, q, r, s):
+    """The string Print-LCS (§I.D) traces for X = a^p b^q, Y = b^r a^s. A common subsequence is a^k or b^k (X has
+    its a's first, Y its b's), so with A = min(p, s) and B = min(q, r) the LCS is unique unless A = B. On a tie the
+    walk starts at (m, n) on a mismatch (x_m = b, y_n = a) whose up and left neighbours both hold A, so it steps
+    up; down column n every neighbour pair stays tied or favours up until row p, where x_p = y_n = a, and from there
+    it matches a's on the diagonal: a^A."""
+    A, B = min(p, s), min(q, r)
+    return b"A" * A if A >= B else b"B" * B
+
+
+def test_runs_closed_form_strings(oracle):
+    """The traced string of the two-run closed form, every (p, q, r, s) in 0..5 (ties included), and the carry that
+    ripples along the whole first row: X = a^m against Y = a b^(n-1) (and the mirror image)."""
+    for p in range(6):
+        for q in range(6):
+            for r in range(6):
+                for s in range(6):
+                    x = b"A" * p + b"B" * q
+                    y = b"B" * r + b"A" * s
+                    assert oracle.lcs_traceback(x, y) == runs_lcs_string(p, q, r, s), (p, q, r, s)
+    for m, n in [(1, 1), (1, 70), (9, 70), (70, 3)]:
+        assert oracle.lcs_traceback(b"A" * m, b"A" + b"B" * (n - 1)) == b"A"
+        assert oracle.lcs_traceback(b"A" * m, b"B" * (n - 1) + b"A") == b"A"
+
+
 def test_theorem_case1_append(oracle):
     """Optimal substructure case 1 (§I.A): if x_m = y_n the LCS is an LCS of the prefixes plus that symbol."""
     for seed in range(5):
