@@ -79,7 +79,7 @@ class ClockSampler:
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-         "clocks_event_reasons.sw_power_cap")
+         "clocks_event_reasons.sw_power_cap,utilization.gpu")
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
@@ -111,7 +111,7 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, mx, pw, reasons = [], [], [], set()
+        sm, mx, pw, util, reasons = [], [], [], [], set()
         names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             p = [v.strip() for v in ln.split(",")]
@@ -121,6 +121,7 @@ class ClockSampler:
                 sm.append(float(p[1]))
                 mx.append(float(p[2]))
                 pw.append(float(p[3]))
+                util.append(float(p[9]) if len(p) > 9 else float("nan"))
             except ValueError:
                 continue
             for k, name in enumerate(names[1:], start=5):
@@ -128,7 +129,8 @@ class ClockSampler:
                     reasons.add(name)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm),
-                "power_w_max": max(pw) if pw else None}
+                "power_w_max": max(pw) if pw else None,
+                "gpu_util_pct_median": float(np.nanmedian(util)) if util and not np.all(np.isnan(util)) else None}
 
 
 def dist_env():
@@ -776,6 +778,18 @@ def run_batch_workload(args):
 
 # ---- serving --------------------------------------------------------------------------------------------------------
 
+SERVE_CLASSES = ("short", "long", "traceback")
+
+
+def serve_class(r: dict) -> str:
+    """The server's routing of a request: tracebacks and long length-only pairs to the single-pair workers, short
+    length-only pairs (shorter side <= 4096, longer side <= 16384, m*n < 2^24) to the batch workers."""
+    m, n = len(r["x"]), len(r["y"])
+    if r["traceback"]:
+        return "traceback"
+    return "short" if min(m, n) <= 4096 and max(m, n) <= 16384 and m * n < (1 << 24) else "long"
+
+
 def measure_serve(args, dev) -> dict:
     """Poisson request streams at swept rates (m and n log-uniform in [32, 65536], alphabet 4, 20 or 256, 20%
     traceback) through the server: latency from submit to result (measured by the server), p50/p99 and served GCUPS
@@ -816,9 +830,14 @@ def measure_serve(args, dev) -> dict:
         wall = time.perf_counter() - t0
         srv.close()
         lat = np.array(lat)
+        cls = np.array([serve_class(r) for r in reqs])
         out_rates.append({"rate_per_s": rate, "requests": len(reqs), "p50_ms": float(np.percentile(lat, 50) * 1e3),
                           "p99_ms": float(np.percentile(lat, 99) * 1e3), "gcups": cells / wall / 1e9,
-                          "offered_gcups": cells / (reqs[-1]["t"] - reqs[0]["t"]) / 1e9, "wall_s": wall})
+                          "offered_gcups": cells / (reqs[-1]["t"] - reqs[0]["t"]) / 1e9, "wall_s": wall,
+                          "by_class": {c: {"requests": int((cls == c).sum()),
+                                           "p50_ms": float(np.percentile(lat[cls == c], 50) * 1e3),
+                                           "p99_ms": float(np.percentile(lat[cls == c], 99) * 1e3)}
+                                       for c in SERVE_CLASSES if (cls == c).any()}})
         print(json.dumps({"serve_rate": out_rates[-1]}), file=sys.stderr, flush=True)
         del reqs
     clocks = sampler.stop()
@@ -831,16 +850,23 @@ def measure_serve(args, dev) -> dict:
         svc.append(time.perf_counter() - t1)
     svc = np.array(svc)
     ctx.close()
+    cls = np.array([serve_class(r) for r in reqs])
     best = max(out_rates, key=lambda d: d["gcups"])
     return {
         "workload": "serving: Poisson arrivals, m,n log-uniform [32, 65536], sigma 4/20/256, 20% traceback",
         "value": best["gcups"], "unit": "GCUPS", "rates": out_rates,
-        "pair_workers": args.pair_workers or 8,
+        "pair_workers": args.pair_workers or 16,
         "per_pair_baseline": {"p50_ms": float(np.percentile(svc, 50) * 1e3),
                               "p99_ms": float(np.percentile(svc, 99) * 1e3),
                               "gcups": sum(len(r["x"]) * len(r["y"]) for r in reqs) / svc.sum() / 1e9,
                               "requests": len(reqs),
+                              "by_class": {c: {"requests": int((cls == c).sum()),
+                                               "p50_ms": float(np.percentile(svc[cls == c], 50) * 1e3),
+                                               "p99_ms": float(np.percentile(svc[cls == c], 99) * 1e3)}
+                                           for c in SERVE_CLASSES if (cls == c).any()},
                               "note": "each request alone through lcs_length / lcs_traceback, one at a time"},
+        "classes": "short: length only, shorter side <= 4096, longer side <= 16384 and m*n < 2^24 (batched); long: "
+                   "other length-only requests; traceback: every request with traceback",
         "clocks": clocks,
     }
 

@@ -253,10 +253,14 @@ typedef struct lcs_server lcs_server;
 
 typedef struct lcs_serve_cfg {
   uint32_t max_queue;          /* requests waiting or in flight before submit returns LCS_ERR_BUSY (0 = 65536) */
-  uint32_t max_batch;          /* short pairs packed into one batched launch (0 = 4096) */
-  uint64_t hbm_budget_bytes;   /* device bytes the server may hold for traceback bitmaps (0 = 60% of free) */
-  uint32_t long_pair_cells_log2; /* pairs with m*n >= 2^this run on the single-pair path (0 = 2^24) */
-  uint32_t pair_workers;       /* single-pair workers, each with its own stream and buffers (0 = 8, at most 32) */
+  uint32_t max_batch;          /* short pairs packed into one batched launch (0 = 4096); a wave also holds at most
+                                  8 MiB of X and 2 MiB of Y symbols */
+  uint64_t hbm_budget_bytes;   /* device bytes of the arena that holds the direction bitmaps of the tracebacks in
+                                  flight, allocated at creation (0 = one 65536 x 65536 bitmap per pair worker, at
+                                  most 60% of free memory). A traceback waits until its bitmap fits the arena */
+  uint32_t long_pair_cells_log2; /* length-only pairs with m*n >= 2^this, or whose shorter side exceeds 4096 or
+                                    longer side 16384, run on the single-pair path (0 = 2^24) */
+  uint32_t pair_workers;       /* single-pair workers, each with its own stream and buffers (0 = 16, at most 32) */
 } lcs_serve_cfg;
 
 typedef struct lcs_result {
@@ -269,7 +273,9 @@ typedef struct lcs_result {
 } lcs_result;
 
 /* Creates a server on ctx (the server then owns the context's streams until lcs_serve_destroy; do not call other
- * functions on ctx meanwhile). cfg may be NULL for defaults. */
+ * functions on ctx meanwhile). cfg may be NULL for defaults. Every device buffer the server uses is allocated here
+ * (the workers' buffers for pairs of up to 65536 x 65536 and the bitmap arena), so that serving requests of those
+ * sizes allocates no device memory. Errors: LCS_ERR_NOMEM, LCS_ERR_CUDA, LCS_ERR_INVALID. */
 LCS_API int lcs_serve_create(lcs_ctx* ctx, const lcs_serve_cfg* cfg, lcs_server** out);
 
 /* Copies x and y and queues the request; *ticket identifies it. Errors: LCS_ERR_BUSY (queue full),

@@ -8,6 +8,8 @@
 
 #include "lcs_ctx.h"
 
+int ensure_hstage(lcs_ctx* c, size_t bytes);  // below: the pinned staging area of a context
+
 using namespace lcs;
 
 extern "C" const char* lcs_strerror(int status) {
@@ -162,30 +164,56 @@ static int run_small(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* 
   return rc;
 }
 
+// Geometry of a length-only call. Meet in the middle: the top half of the rows forward, the bottom half on the
+// reversed strings, at the same time; L = max_j (c[mt, j] + LCS(X[mt+1..m], Y[j+1..n])) (the recurrence read from
+// both ends).
+struct LenGeo {
+  uint32_t B;
+  Geo g;
+  bool split;
+  uint64_t mt, mb, Rf, padr, Rr;
+};
+static LenGeo len_geo(const lcs_ctx* c, uint64_t m, uint64_t n) {
+  LenGeo L;
+  L.B = c->fill_B;
+  L.g = geo_for(n);
+  L.split = m >= 2 * L.B && 2 * L.g.nblocks <= (uint64_t)c->max_coop;
+  L.mt = L.split ? L.B * (m / (2 * L.B)) : m;
+  L.mb = m - L.mt;
+  L.Rf = (L.mt + L.B - 1) / L.B;
+  L.padr = L.split ? (L.B - L.mb % L.B) % L.B : 0;
+  L.Rr = L.split ? (L.mb + L.padr) / L.B : 0;
+  return L;
+}
+
+// Every device buffer a length-only call of this geometry uses (grow-only).
+static int ensure_len(lcs_ctx* c, const LenGeo& L) {
+  const uint32_t B = L.B;
+  const Geo& g = L.g;
+  int rc = from_cuda(ensure(c->peq_f, (size_t)kSigmaMax * g.wpad * 4));
+  if (!rc && L.split) rc = from_cuda(ensure(c->peq_r, (size_t)kSigmaMax * g.wpad * 4));
+  if (!rc) rc = from_cuda(ensure(c->xoff_f, (L.Rf + kPadRowblocks + kPadBackRowblocks) * B * 4));
+  if (!rc) rc = from_cuda(ensure(c->carry_f, g.nblocks * L.Rf * 4));
+  if (!rc) rc = from_cuda(ensure(c->fv_f, g.wpad * 4));
+  if (!rc && L.split) rc = from_cuda(ensure(c->xoff_r, (L.Rr + kPadRowblocks + kPadBackRowblocks) * B * 4));
+  if (!rc && L.split) rc = from_cuda(ensure(c->carry_r, g.nblocks * L.Rr * 4));
+  if (!rc && L.split) rc = from_cuda(ensure(c->fv_r, g.wpad * 4));
+  if (!rc && L.split) rc = from_cuda(ensure(c->colsum, (2 * (g.wq + 1) + 4) * 4));
+  return rc;
+}
+
 int run_length(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, uint64_t n, uint64_t* d_out,
                cudaStream_t st) {
   if (m == 0 || n == 0) return from_cuda(cudaMemsetAsync(d_out, 0, sizeof(uint64_t), st));
   if (c->small_path && small_pair(m, n)) return run_small(c, d_x, m, d_y, n, false, nullptr, 0, d_out, st);
-  const uint32_t B = c->fill_B;
-  const Geo g = geo_for(n);
-  // Meet in the middle: the top half of the rows forward, the bottom half on the reversed strings, at the same
-  // time; L = max_j (c[mt, j] + LCS(X[mt+1..m], Y[j+1..n])) (the recurrence read from both ends).
-  const bool split = m >= 2 * B && 2 * g.nblocks <= (uint64_t)c->max_coop;
-  const uint64_t mt = split ? B * (m / (2 * B)) : m;
-  const uint64_t mb = m - mt;
-  const uint64_t Rf = (mt + B - 1) / B;
-  const uint64_t padr = split ? (B - mb % B) % B : 0;
-  const uint64_t Rr = split ? (mb + padr) / B : 0;
+  const LenGeo LG = len_geo(c, m, n);
+  const uint32_t B = LG.B;
+  const Geo& g = LG.g;
+  const bool split = LG.split;
+  const uint64_t mt = LG.mt, mb = LG.mb, Rf = LG.Rf, padr = LG.padr, Rr = LG.Rr;
   c->mark(0, st);
-  int rc = prep_y(c, d_y, n, g, split, st);
-  if (rc) return rc;
-  rc = from_cuda(ensure(c->xoff_f, (Rf + kPadRowblocks + kPadBackRowblocks) * B * 4));
-  if (!rc) rc = from_cuda(ensure(c->carry_f, g.nblocks * Rf * 4));
-  if (!rc) rc = from_cuda(ensure(c->fv_f, g.wpad * 4));
-  if (!rc && split) rc = from_cuda(ensure(c->xoff_r, (Rr + kPadRowblocks + kPadBackRowblocks) * B * 4));
-  if (!rc && split) rc = from_cuda(ensure(c->carry_r, g.nblocks * Rr * 4));
-  if (!rc && split) rc = from_cuda(ensure(c->fv_r, g.wpad * 4));
-  if (!rc && split) rc = from_cuda(ensure(c->colsum, (2 * (g.wq + 1) + 4) * 4));
+  int rc = ensure_len(c, LG);
+  if (!rc) rc = prep_y(c, d_y, n, g, split, st);
   if (rc) return rc;
   {  // row offsets of both tables; the hand-off slots and the length accumulator start at zero
     const XoffJob xj[2] = {{d_x, mt, 0, 0, Rf, (uint32_t*)c->xoff_f.p, nullptr},
@@ -231,44 +259,89 @@ int run_length(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, u
   return rc;
 }
 
-int run_traceback(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, uint64_t n, uint8_t* d_out,
-                  uint64_t out_cap, uint64_t* d_out_len, cudaStream_t st) {
-  if (m == 0 || n == 0) return from_cuda(cudaMemsetAsync(d_out_len, 0, sizeof(uint64_t), st));
-  if (c->small_path && small_pair(m, n)) return run_small(c, d_x, m, d_y, n, true, d_out, out_cap, d_out_len, st);
-  const uint32_t B = c->fill_B_tb;
-  const Geo g = geo_for(n);
-  // Segments of H rows for the parallel walk, at most kMaxSegments of them. H is a multiple of 32 * B: the fill
-  // kernel snapshots a lane's word once per 32 steps.
-  const uint64_t unit = 32ull * B;
-  const uint64_t H = unit * ((m + kMaxSegments * unit - 1) / (kMaxSegments * unit));
-  const uint64_t S = (m + H - 1) / H;
-  const bool rev = S > 1;
-  const uint64_t Rf = (m + B - 1) / B;
-  const uint64_t padr = S * H - m;
-  const uint64_t Rr = rev ? (S * H) / B : 0;
-  const uint64_t nwarps = g.nblocks * kFillWarps;
-  const size_t t_bytes = (size_t)nwarps * (Rf + 31) * 32 * B * 4;
-  c->mark(0, st);
-  int rc = prep_y(c, d_y, n, g, rev, st);
-  if (rc) return rc;
-  rc = from_cuda(ensure(c->T, t_bytes));
-  if (!rc) rc = from_cuda(ensure(c->xoff_f, (Rf + kPadRowblocks + kPadBackRowblocks) * B * 4));
-  if (!rc) rc = from_cuda(ensure(c->xcode, m));
-  if (!rc) rc = from_cuda(ensure(c->carry_f, g.nblocks * Rf * 4));
-  if (!rc) rc = from_cuda(ensure(c->snap_f, S * g.wpad * 4));
-  if (!rc && rev) rc = from_cuda(ensure(c->xoff_r, (Rr + kPadRowblocks + kPadBackRowblocks) * B * 4));
-  if (!rc && rev) rc = from_cuda(ensure(c->carry_r, g.nblocks * Rr * 4));
-  if (!rc && rev) rc = from_cuda(ensure(c->snap_r, S * g.wpad * 4));
-  if (!rc) rc = from_cuda(ensure(c->colsum, (S * 2 * (g.wq + 1) + 4) * 4));
+// Geometry of a traceback call. Segments of H rows for the parallel walk, at most kMaxSegments of them. H is a
+// multiple of 32 * B: the fill kernel snapshots a lane's word once per 32 steps.
+struct TbGeo {
+  uint32_t B;
+  Geo g;
+  uint64_t H, S, Rf, padr, Rr, W;
+  bool rev;
+  size_t t_bytes;  // the direction bitmap
+};
+static TbGeo tb_geo(const lcs_ctx* c, uint64_t m, uint64_t n) {
+  TbGeo T;
+  T.B = c->fill_B_tb;
+  T.g = geo_for(n);
+  const uint64_t unit = 32ull * T.B;
+  T.H = unit * ((m + kMaxSegments * unit - 1) / (kMaxSegments * unit));
+  T.S = (m + T.H - 1) / T.H;
+  T.rev = T.S > 1;
+  T.Rf = (m + T.B - 1) / T.B;
+  T.padr = T.S * T.H - m;
+  T.Rr = T.rev ? (T.S * T.H) / T.B : 0;
+  const uint64_t nwarps = T.g.nblocks * kFillWarps;
+  T.t_bytes = (size_t)nwarps * (T.Rf + 31) * 32 * T.B * 4;
   // walkers per segment: as many as the corridor can have columns (n + 1), within the budget
-  uint64_t W = std::min<uint64_t>(n + 1, std::min<uint64_t>(kMaxWalkersPerSeg, kWalkerBudget / S));
-  W = std::max<uint64_t>(kWalkers, (W + kWalkers - 1) / kWalkers * kWalkers);
+  uint64_t W = std::min<uint64_t>(n + 1, std::min<uint64_t>(kMaxWalkersPerSeg, kWalkerBudget / T.S));
+  T.W = std::max<uint64_t>(kWalkers, (W + kWalkers - 1) / kWalkers * kWalkers);
+  return T;
+}
+
+// Every device buffer a traceback call of this geometry uses (grow-only), the bitmap only when with_T.
+static int ensure_tb(lcs_ctx* c, const TbGeo& T, uint64_t m, bool with_T) {
+  const uint32_t B = T.B;
+  const Geo& g = T.g;
+  const uint64_t S = T.S, W = T.W;
+  int rc = from_cuda(ensure(c->peq_f, (size_t)kSigmaMax * g.wpad * 4));
+  if (!rc && T.rev) rc = from_cuda(ensure(c->peq_r, (size_t)kSigmaMax * g.wpad * 4));
+  if (!rc && with_T) rc = from_cuda(ensure(c->T, T.t_bytes));
+  if (!rc) rc = from_cuda(ensure(c->xoff_f, (T.Rf + kPadRowblocks + kPadBackRowblocks) * B * 4));
+  if (!rc) rc = from_cuda(ensure(c->xcode, m));
+  if (!rc) rc = from_cuda(ensure(c->carry_f, g.nblocks * T.Rf * 4));
+  if (!rc) rc = from_cuda(ensure(c->snap_f, S * g.wpad * 4));
+  if (!rc && T.rev) rc = from_cuda(ensure(c->xoff_r, (T.Rr + kPadRowblocks + kPadBackRowblocks) * B * 4));
+  if (!rc && T.rev) rc = from_cuda(ensure(c->carry_r, g.nblocks * T.Rr * 4));
+  if (!rc && T.rev) rc = from_cuda(ensure(c->snap_r, S * g.wpad * 4));
+  if (!rc) rc = from_cuda(ensure(c->colsum, (S * 2 * (g.wq + 1) + 4) * 4));
   if (!rc) rc = from_cuda(ensure(c->ent, S * W * 4));
   if (!rc) rc = from_cuda(ensure(c->ext, S * W * 4));
   if (!rc) rc = from_cuda(ensure(c->nch, S * W * 4));
   if (!rc) rc = from_cuda(ensure(c->entcnt, S * 4));
   if (!rc) rc = from_cuda(ensure(c->sel, S * 4));
-  if (!rc) rc = from_cuda(ensure(c->chars, S * (W + 1) * H));
+  if (!rc) rc = from_cuda(ensure(c->chars, S * (W + 1) * T.H));
+  return rc;
+}
+
+uint64_t traceback_bitmap_bytes(const lcs_ctx* c, uint64_t m, uint64_t n) {
+  if (m == 0 || n == 0 || (c->small_path && small_pair(m, n))) return 0;
+  return tb_geo(c, m, n).t_bytes;
+}
+
+// Grows every buffer a length-only or traceback call with m <= max_m and n <= max_n uses, except the traceback's
+// direction bitmap, so that such calls allocate nothing (the growth keeps a margin for the few shapes whose
+// walker buffers exceed those of (max_m, max_n) slightly).
+int presize(lcs_ctx* c, uint64_t max_m, uint64_t max_n) {
+  int rc = ensure_len(c, len_geo(c, max_m, max_n));
+  if (!rc) rc = ensure_tb(c, tb_geo(c, max_m, max_n), max_m, false);
+  if (!rc) rc = from_cuda(ensure(c->x, std::max<uint64_t>(max_m, 1)));
+  if (!rc) rc = from_cuda(ensure(c->y, std::max<uint64_t>(max_n, 1)));
+  if (!rc) rc = from_cuda(ensure(c->out, std::max<uint64_t>(std::min(max_m, max_n), 1)));
+  if (!rc) rc = ensure_hstage(c, max_m + max_n);
+  return rc;
+}
+
+int run_traceback(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, uint64_t n, uint8_t* d_out,
+                  uint64_t out_cap, uint64_t* d_out_len, cudaStream_t st) {
+  if (m == 0 || n == 0) return from_cuda(cudaMemsetAsync(d_out_len, 0, sizeof(uint64_t), st));
+  if (c->small_path && small_pair(m, n)) return run_small(c, d_x, m, d_y, n, true, d_out, out_cap, d_out_len, st);
+  const TbGeo TG = tb_geo(c, m, n);
+  const uint32_t B = TG.B;
+  const Geo& g = TG.g;
+  const uint64_t H = TG.H, S = TG.S, Rf = TG.Rf, padr = TG.padr, Rr = TG.Rr, W = TG.W;
+  const bool rev = TG.rev;
+  c->mark(0, st);
+  int rc = ensure_tb(c, TG, m, true);
+  if (!rc) rc = prep_y(c, d_y, n, g, rev, st);
   if (rc) return rc;
   {  // row offsets of both tables; hand-off slots, length accumulator and corridor counts start at zero
     const XoffJob xj[2] = {{d_x, m, 0, 0, Rf, (uint32_t*)c->xoff_f.p, (uint8_t*)c->xcode.p},

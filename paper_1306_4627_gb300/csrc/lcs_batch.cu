@@ -590,7 +590,10 @@ static cudaError_t batch_launches(lcs_ctx* c, uint64_t* d_out, uint64_t count, c
     const unsigned prep_blocks = (unsigned)std::min<uint64_t>((a.npairs + 7) / 8, sms * c->b_prep_per_sm);
     k_batch_prep<<<prep_blocks, 256, 0, st>>>(a);
     const uint32_t k_max = a.stage_words / (32u * kStageRows);
-    const unsigned blocks = (unsigned)(sms * batch_blocks_per_sm(c, c->b_main_occ_k[k_index(k_max)]));
+    // persistent blocks: one wave over the SMs, but no more than the items need (a small batch then starts at
+    // once on the SMs that are free instead of waiting for blocks that would find no work)
+    const unsigned blocks = (unsigned)std::min<uint64_t>(sms * batch_blocks_per_sm(c, c->b_main_occ_k[k_index(k_max)]),
+                                                         (a.nitems + kBatchWarps - 1) / kBatchWarps);
     if (marks) c->mark(1, st);
     k_batch_main<<<blocks, kBatchWarps * 32, main_smem_bytes(k_max), st>>>(a);
     if (a.nsplit) k_batch_combine<<<(unsigned)std::min<uint64_t>((a.nsplit + 7) / 8, sms * 8), 256, 0, st>>>(a);
@@ -646,6 +649,41 @@ static int upload_plan(lcs_ctx* c, const Plan& plan, size_t jat, size_t iat, siz
   if (!rc) rc = from_cuda(cudaMemcpyAsync(base + iat, plan.items.data(), ib, cudaMemcpyHostToDevice, st));
   if (!rc && sb) rc = from_cuda(cudaMemcpyAsync(base + sat, plan.split.data(), sb, cudaMemcpyHostToDevice, st));
   if (!rc) rc = from_cuda(cudaMemcpyAsync(base + oat, plan.prep_order.data(), ob, cudaMemcpyHostToDevice, st));
+  return rc;
+}
+
+// Grows every buffer a host-buffer batch call (lcs_batch) uses for batches of at most max_pairs pairs with at most
+// x_bytes symbols of X and y_bytes of Y in all, every y at most 4096 symbols, so that such calls allocate nothing:
+// the plan and its pinned upload buffer, the alphabet sizes, the padded code lists (every pair's list padded at both
+// ends and aligned, twice for a split pair), the match-mask tables (at most (256 + 1) * ceil(n / 32) words per pair,
+// twice for a split pair: under 17 words per symbol of Y plus 520 per pair), the split pairs' final rows, the
+// device copies of the inputs and the lengths, and the pinned staging area.
+int batch_presize(lcs_ctx* c, uint64_t max_pairs, uint64_t x_bytes, uint64_t y_bytes) {
+  int rc = from_cuda(batch_geometry(c));
+  const uint64_t P = std::max<uint64_t>(max_pairs, 1);
+  const size_t plan_bytes = P * sizeof(BPair) + 2 * P * sizeof(BJob) + 2 * P * sizeof(BItem) + 2 * P * 4 + 6 * 256;
+  const uint64_t codes = kCodeZeros + x_bytes + 2 * P * (kCodePadFront + 15 + kCodePadBack);
+  if (!rc) rc = from_cuda(ensure(c->bplan, plan_bytes));
+  if (!rc) rc = from_cuda(ensure(c->bsig, P * 4 + 4));
+  if (!rc) rc = from_cuda(ensure(c->bxcode, (codes + 16) * 2));
+  if (!rc) rc = from_cuda(ensure(c->bpeq, (17 * y_bytes + 520 * P + 4) * 4));
+  if (!rc) rc = from_cuda(ensure(c->bfv, ((uint64_t)2 * P * kRowWords + 4) * 4));
+  if (!rc) rc = from_cuda(ensure(c->x, std::max<uint64_t>(x_bytes, 1)));
+  if (!rc) rc = from_cuda(ensure(c->y, std::max<uint64_t>(y_bytes, 1)));
+  if (!rc) rc = from_cuda(ensure(c->bout, P * 8));
+  if (!rc) rc = ensure_hstage(c, x_bytes + y_bytes + P * 8 + 8);
+  if (!rc && plan_bytes > c->hplan_cap) {
+    if (c->hplan_ev) cudaEventSynchronize(c->hplan_ev);
+    if (c->hplan) cudaFreeHost(c->hplan);
+    c->hplan = nullptr;
+    c->hplan_cap = 0;
+    void* p = nullptr;
+    rc = from_cuda(cudaMallocHost(&p, plan_bytes));
+    if (!rc) {
+      c->hplan = static_cast<uint8_t*>(p);
+      c->hplan_cap = plan_bytes;
+    }
+  }
   return rc;
 }
 
