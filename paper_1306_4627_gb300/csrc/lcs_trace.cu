@@ -266,10 +266,16 @@ __device__ uint64_t walk_segment(const TraceArgs& a, uint64_t hi, uint64_t lo, u
   return j;
 }
 
-// The same walk done by a whole warp (all lanes call it with the same arguments and follow the same path): lane k
-// fetches the words of row i - k at the walk's current 32-column word, so the loads of 32 rows overlap, and the
-// walk takes them from the lanes one row at a time; when it moves to another word it fetches again from that row
-// (one round of loads instead of one load per remaining row). Lane 0 writes the emitted symbols.
+// The same walk done by a whole warp (all lanes call it with the same arguments and follow the same path). Each
+// round fetches the words of kWalkRounds * 32 rows at the walk's current 32-column word (lane k, slot r: row
+// i - 32 r - k), so the loads of all those rows are in flight together. Most rows of a walk step UP at the walk's
+// column without a match (nearly all of them for a tall pair, whose path is mostly vertical); such a row changes
+// nothing but i. So the warp takes one ballot of "this row's cell at column j is a match or a LEFT cell" over the
+// 32 rows of a slot and jumps straight to the first such row; only those rows are worked one by one (their words
+// taken from their lane by shuffles). When the walk moves to another word it fetches again from that row. Lane 0
+// writes the emitted symbols (when out_chars is not null).
+constexpr int kWalkRounds = 4;
+
 __device__ uint64_t walk_segment_warp(const TraceArgs& a, uint64_t hi, uint64_t lo, uint64_t e, uint8_t* out_chars,
                                       uint32_t* out_cnt) {
   const uint32_t lane = threadIdx.x & 31;
@@ -277,70 +283,84 @@ __device__ uint64_t walk_segment_warp(const TraceArgs& a, uint64_t hi, uint64_t 
   uint32_t cnt = 0;
   while (i > lo && j > 0) {
     const int64_t Qg = (int64_t)(j >> 5);
-    const bool ok = i > lo + lane;
-    const uint32_t cd = ok ? a.xcode[i - lane - 1] : 0u;
-    const uint32_t xs = ok ? a.x[i - lane - 1] : 0u;
-    const uint32_t dv = ok ? t_word(a, i - lane, (uint64_t)Qg) : 0u;
-    const uint32_t pa = ok ? p_word(a, cd, Qg) : 0u;
-    const uint32_t pb = ok ? p_word(a, cd, Qg - 1) : 0u;
-    // row k's words are taken from lane k one row ahead of their use
-    uint32_t n_code = __shfl_sync(kFull, cd, 0), n_sym = __shfl_sync(kFull, xs, 0);
-    uint32_t n_dk = __shfl_sync(kFull, dv, 0), n_pak = __shfl_sync(kFull, pa, 0), n_pbk = __shfl_sync(kFull, pb, 0);
-    for (uint32_t k = 0; k < 32; ++k) {
-      if (i <= lo || j == 0) break;  // the same on every lane
-      if ((int64_t)(j >> 5) != Qg) break;  // the walk left the fetched word: fetch again from this row, at its word
-      const uint32_t code = n_code, sym = n_sym, dk = n_dk, pak = n_pak, pbk = n_pbk;
-      const uint32_t kn = (k + 1) & 31;
-      n_code = __shfl_sync(kFull, cd, kn);
-      n_sym = __shfl_sync(kFull, xs, kn);
-      n_dk = __shfl_sync(kFull, dv, kn);
-      n_pak = __shfl_sync(kFull, pa, kn);
-      n_pbk = __shfl_sync(kFull, pb, kn);
-      int64_t Q = (int64_t)(j >> 5);
-      if (Q == Qg) {  // most rows stop at column j itself (an UP or a match there): no bit scan
+    const uint64_t i0 = i;
+    uint32_t cd[kWalkRounds], xs[kWalkRounds], dv[kWalkRounds], pm[kWalkRounds];
+    bool okr[kWalkRounds];
+#pragma unroll
+    for (int r = 0; r < kWalkRounds; ++r) {
+      const uint64_t off = 32ull * r + lane;  // this lane's row of slot r: i0 - off
+      okr[r] = i0 > lo + off;
+      cd[r] = okr[r] ? a.xcode[i0 - off - 1] : 0u;
+      xs[r] = okr[r] ? a.x[i0 - off - 1] : 0u;
+      dv[r] = okr[r] ? t_word(a, i0 - off, (uint64_t)Qg) : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < kWalkRounds; ++r) {  // bit b of pm: a match at column 32 Qg + b
+      const uint32_t pa = okr[r] ? p_word(a, cd[r], Qg) : 0u;
+      const uint32_t pb = okr[r] ? p_word(a, cd[r], Qg - 1) : 0u;
+      pm[r] = (pa << 1) | (pb >> 31);
+    }
+    bool leave = false;  // the walk ended, or left the fetched word (same value on every lane)
+#pragma unroll
+    for (int r = 0; r < kWalkRounds; ++r) {
+      if (leave) break;
+      // invariant: i = i0 - (32 r + k)
+      for (uint32_t k = 0; k < 32;) {
+        if (i <= lo || j == 0 || (int64_t)(j >> 5) != Qg) {
+          leave = true;
+          break;
+        }
         const uint32_t bj = (uint32_t)(j & 31);
-        const uint32_t pmj = (bj ? (pak >> (bj - 1)) : (pbk >> 31)) & 1u;
-        if (((dk >> bj) & 1u) == 0u || pmj) {
-          if (pmj) {
-            if (lane == 0) out_chars[cnt] = (uint8_t)sym;
-            ++cnt;
-            --j;
+        // rows past the segment count as events too: the walk stops there
+        const bool evl = !okr[r] || (((dv[r] | pm[r]) >> bj) & 1u);
+        const uint32_t ev = __ballot_sync(kFull, evl) & (kFull << k);
+        if (!ev) {  // every remaining row of the slot steps UP at column j
+          i -= 32 - k;
+          break;
+        }
+        const uint32_t kk = (uint32_t)__ffs(ev) - 1;
+        i -= kk - k;
+        k = kk;
+        if (i <= lo) {
+          leave = true;
+          break;
+        }
+        const uint32_t code = __shfl_sync(kFull, cd[r], kk), sym = __shfl_sync(kFull, xs[r], kk);
+        const uint32_t dk = __shfl_sync(kFull, dv[r], kk), pmk = __shfl_sync(kFull, pm[r], kk);
+        if ((pmk >> bj) & 1u) {  // a match at column j: DIAG
+          if (out_chars && lane == 0) out_chars[cnt] = (uint8_t)sym;
+          ++cnt;
+          --j;
+        } else {  // a LEFT cell: the first column c < j with a match or an UP cell
+          int64_t Q = Qg;
+          uint32_t mask = kFull >> (31 - bj), d = dk, pq = pmk, stop = 0;
+          for (;;) {
+            stop = (pq | ~d) & mask;
+            if (Q == 0) stop &= ~1u;  // column 0 is the border
+            if (stop || Q == 0) break;
+            --Q;
+            mask = kFull;
+            d = t_word(a, i, (uint64_t)Q);
+            pq = (p_word(a, code, Q) << 1) | (p_word(a, code, Q - 1) >> 31);
           }
-          --i;
-          continue;
+          if (!stop) {
+            j = 0;
+            leave = true;
+            break;
+          }
+          const uint32_t bit = 31u - __clz(stop);
+          const uint64_t c = ((uint64_t)Q << 5) + bit;
+          if ((pq >> bit) & 1u) {
+            if (out_chars && lane == 0) out_chars[cnt] = (uint8_t)sym;
+            ++cnt;
+            j = c - 1;
+          } else {
+            j = c;
+          }
         }
+        --i;
+        ++k;
       }
-      uint32_t mask = kFull >> (31 - (uint32_t)(j & 31));
-      uint32_t pm = 0, stop = 0;
-      for (;;) {
-        uint32_t d;
-        if (Q == Qg) {
-          d = dk;
-          pm = (pak << 1) | (pbk >> 31);
-        } else {
-          d = t_word(a, i, (uint64_t)Q);
-          pm = (p_word(a, code, Q) << 1) | (p_word(a, code, Q - 1) >> 31);
-        }
-        stop = (pm | ~d) & mask;
-        if (Q == 0) stop &= ~1u;
-        if (stop || Q == 0) break;
-        --Q;
-        mask = kFull;
-      }
-      if (!stop) {
-        j = 0;
-        break;
-      }
-      const uint32_t bit = 31u - __clz(stop);
-      const uint64_t c = ((uint64_t)Q << 5) + bit;
-      if ((pm >> bit) & 1u) {
-        if (lane == 0) out_chars[cnt] = (uint8_t)sym;
-        ++cnt;
-        j = c - 1;
-      } else {
-        j = c;
-      }
-      --i;
     }
   }
   *out_cnt = cnt;
