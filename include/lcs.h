@@ -275,7 +275,10 @@ typedef struct lcs_result {
 /* Creates a server on ctx (the server then owns the context's streams until lcs_serve_destroy; do not call other
  * functions on ctx meanwhile). cfg may be NULL for defaults. Every device buffer the server uses is allocated here
  * (the workers' buffers for pairs of up to 65536 x 65536 and the bitmap arena), so that serving requests of those
- * sizes allocates no device memory. Errors: LCS_ERR_NOMEM, LCS_ERR_CUDA, LCS_ERR_INVALID. */
+ * sizes allocates no device memory. The workers (2 batch workers plus pair_workers) each run their own stream: give
+ * the process at least that many hardware work queues by setting the environment variable
+ * CUDA_DEVICE_MAX_CONNECTIONS (e.g. to 32) before its first CUDA call; with the runtime's default of 8, workers
+ * share queues and wait on each other's kernels. Errors: LCS_ERR_NOMEM, LCS_ERR_CUDA, LCS_ERR_INVALID. */
 LCS_API int lcs_serve_create(lcs_ctx* ctx, const lcs_serve_cfg* cfg, lcs_server** out);
 
 /* Copies x and y and queues the request; *ticket identifies it. Errors: LCS_ERR_BUSY (queue full),

@@ -67,13 +67,38 @@ void release(DBuf& b) {
   b.cap = 0;
 }
 
+// Waits for the context's stream: a spin wait by default, or a blocking wait on an event for contexts that set
+// blocking_wait (the server's workers), which sleeps instead of spinning.
+int wait_stream(lcs_ctx* c) {
+  if (!c->blocking_wait) return from_cuda(cudaStreamSynchronize(c->stream));
+  int rc = LCS_OK;
+  if (!c->wait_ev) rc = from_cuda(cudaEventCreateWithFlags(&c->wait_ev, cudaEventBlockingSync | cudaEventDisableTiming));
+  if (!rc) rc = from_cuda(cudaEventRecord(c->wait_ev, c->stream));
+  if (!rc) rc = from_cuda(cudaEventSynchronize(c->wait_ev));
+  return rc;
+}
+
+// Copies the status word back behind the work enqueued on the context's stream, waits for the stream, and returns
+// the latched error (clearing it) or LCS_OK.
+int fetch_status(lcs_ctx* c) {
+  int rc = from_cuda(cudaMemcpyAsync(c->host_tail, (char*)c->small.p + kOffStatus, sizeof(DevStatus),
+                                     cudaMemcpyDeviceToHost, c->stream));
+  if (!rc) rc = wait_stream(c);
+  if (rc) return rc;
+  DevStatus h;
+  std::memcpy(&h, c->host_tail, sizeof(h));
+  if (h.flags == 0) return LCS_OK;
+  cudaMemset(c->status(), 0, sizeof(DevStatus));
+  return (h.flags & kStatTimeout) ? LCS_ERR_TIMEOUT : LCS_ERR_INTERNAL;
+}
+
 // Copies the status word and the result length of the call just enqueued on the context's stream back in one
 // transfer, waits for the stream, and returns the latched error (clearing it) or LCS_OK with *len.
 int fetch_result(lcs_ctx* c, uint64_t* len) {
   static_assert(kOffOutLen > kOffStatus && kOffOutLen - kOffStatus + 8 <= 8 * sizeof(uint64_t), "layout");
   int rc = from_cuda(cudaMemcpyAsync(c->host_tail, (char*)c->small.p + kOffStatus, kOffOutLen - kOffStatus + 8,
                                      cudaMemcpyDeviceToHost, c->stream));
-  if (!rc) rc = from_cuda(cudaStreamSynchronize(c->stream));
+  if (!rc) rc = wait_stream(c);
   if (rc) return rc;
   DevStatus h;
   std::memcpy(&h, c->host_tail, sizeof(h));
@@ -508,6 +533,7 @@ extern "C" void lcs_ctx_destroy(lcs_ctx* c) {
   c->release_all();
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
+  if (c->wait_ev) cudaEventDestroy(c->wait_ev);
   if (c->stream) cudaStreamDestroy(c->stream);
   if (c->host_tail) cudaFreeHost(c->host_tail);
   delete c;

@@ -870,8 +870,7 @@ static int lcs_batch_impl(lcs_ctx* c, const uint8_t* xs, const uint64_t* x_off, 
   uint64_t* land = stage ? reinterpret_cast<uint64_t*>(c->hstage + ((nx + ny + 7) & ~(uint64_t)7)) : out_lens;
   if (stage && (uint8_t*)(land + count) > c->hstage + c->hstage_cap) land = out_lens;
   if (!rc) rc = from_cuda(cudaMemcpyAsync(land, c->bout.p, count * 8, cudaMemcpyDeviceToHost, c->stream));
-  if (!rc) rc = from_cuda(cudaStreamSynchronize(c->stream));
-  if (!rc) rc = take_status(c);
+  if (!rc) rc = fetch_status(c);  // the status word behind the lengths, one wait for both
   if (!rc && land != out_lens) std::memcpy(out_lens, land, count * 8);
   return rc;
 }

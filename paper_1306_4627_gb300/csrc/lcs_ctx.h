@@ -19,6 +19,8 @@ struct DBuf {
 cudaError_t ensure(DBuf& b, size_t bytes);
 void release(DBuf& b);
 int from_cuda(cudaError_t e);
+int wait_stream(lcs_ctx* c);   // waits for the context's stream (spin or blocking wait, see lcs_ctx::blocking_wait)
+int fetch_status(lcs_ctx* c);  // copies the status word back behind the stream's work, waits, returns its error
 
 // Layout of the small control block (bytes).
 constexpr size_t kOffCodemap = 0;      // uint16_t[256]
@@ -51,6 +53,10 @@ struct lcs_ctx {
   uint32_t bk_max = 4;  // the planned batch's largest words per lane
   uint32_t debug_drop = 0;    // test hook (environment LCS_DEBUG_DROP_HANDOFF): a hand-off that never comes
   bool small_path = true;     // small pairs in one launch (lcs_small.cu); environment LCS_NO_SMALL_PATH=1 turns it off
+  // host-buffer calls wait for their stream by a spin (lowest latency) or, when set (the server's workers: many
+  // contexts waiting at once on few host cores), by sleeping on an event recorded with blocking synchronisation
+  bool blocking_wait = false;
+  cudaEvent_t wait_ev = nullptr;
   std::mutex mu;
   lcs::DBuf small, x, y, out;
   lcs::DBuf xoff_f, xoff_r, xcode, peq_f, peq_r, carry_f, carry_r, fv_f, fv_r, T, snap_f, snap_r;

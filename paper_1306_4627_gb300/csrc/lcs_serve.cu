@@ -287,7 +287,10 @@ static int lcs_serve_create_impl(lcs_ctx* ctx, const lcs_serve_cfg* cfg, lcs_ser
     for (uint32_t k = 0; k < kBatchWorkers + s->cfg.pair_workers && !rc; ++k) {
       lcs_ctx* c = nullptr;
       rc = lcs_ctx_create(s->device, &c);
-      if (!rc) s->ctxs.push_back(c);
+      if (!rc) {
+        c->blocking_wait = true;  // many workers, few host cores: wait for the GPU asleep, not spinning
+        s->ctxs.push_back(c);
+      }
     }
     // buffers grown now, so that no request allocates: the batch workers' for their largest wave, every pair
     // worker's for pairs of up to 65536 x 65536
