@@ -334,6 +334,8 @@ static int ensure_tb(lcs_ctx* c, const TbGeo& T, uint64_t m, bool with_T) {
   if (!rc) rc = from_cuda(ensure(c->entcnt, S * 4));
   if (!rc) rc = from_cuda(ensure(c->sel, S * 4));
   if (!rc) rc = from_cuda(ensure(c->chars, S * (W + 1) * T.H));
+  if (!rc) rc = from_cuda(ensure(c->cmap, S * (g.wq * 32 + 1) * sizeof(uint16_t)));  // n + 1 <= 32 wq entries a row
+  if (!rc) rc = from_cuda(ensure(c->wlink, S * W * sizeof(uint16_t)));
   return rc;
 }
 
@@ -417,6 +419,8 @@ int run_traceback(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y
   t.chars = (uint8_t*)c->chars.p;
   t.sel = (uint32_t*)c->sel.p;
   t.colsum = (uint32_t*)c->colsum.p;
+  t.cmap = (uint16_t*)c->cmap.p;
+  t.link = (uint16_t*)c->wlink.p;
   t.out = d_out;
   t.out_len = (unsigned long long*)d_out_len;
   t.out_cap = out_cap;

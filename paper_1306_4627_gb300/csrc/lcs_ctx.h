@@ -60,7 +60,7 @@ struct lcs_ctx {
   std::mutex mu;
   lcs::DBuf small, x, y, out;
   lcs::DBuf xoff_f, xoff_r, xcode, peq_f, peq_r, carry_f, carry_r, fv_f, fv_r, T, snap_f, snap_r;
-  lcs::DBuf colsum, ent, ext, nch, entcnt, sel, chars;
+  lcs::DBuf colsum, ent, ext, nch, entcnt, sel, chars, cmap, wlink;
   lcs::DBuf bplan, bsig, bxcode, bpeq, bout, bfv;  // batch: plan, alphabet sizes, codes, masks, lengths, half rows
   // batch: the last plan's launches captured as a CUDA graph, replayed while the same batch is submitted again
   bool bvalid = false;
@@ -111,7 +111,7 @@ struct lcs_ctx {
     if (cap_stream) cudaStreamDestroy(cap_stream);
     cap_stream = nullptr;
     lcs::DBuf* all[] = {&small, &x, &y, &out, &xoff_f, &xoff_r, &xcode, &peq_f, &peq_r, &carry_f, &carry_r,
-                        &fv_f, &fv_r, &T, &snap_f, &snap_r, &colsum, &ent, &ext, &nch, &entcnt, &sel, &chars,
+                        &fv_f, &fv_r, &T, &snap_f, &snap_r, &colsum, &ent, &ext, &nch, &entcnt, &sel, &chars, &cmap, &wlink,
                         &bplan, &bsig, &bxcode, &bpeq, &bout, &bfv};
     for (lcs::DBuf* b : all) lcs::release(*b);
   }

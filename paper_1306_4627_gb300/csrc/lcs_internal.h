@@ -81,6 +81,8 @@ struct TraceArgs {
   uint8_t* chars;           // [S][W + 1][H] emitted symbols in walk order (slot W: the fallback walk)
   uint32_t* sel;            // [S] selected walker per segment
   uint32_t* colsum;         // scratch [2][S][w+1] word prefix popcounts
+  uint16_t* cmap;           // [S][n+1] column -> walker of the segments with more than 32 walkers (k_corr_map)
+  uint16_t* link;           // [S][W] walker of segment s - 1 that continues walker k of segment s (k_chain_links)
   uint8_t* out;             // LCS output (capacity out_cap)
   unsigned long long* out_len;
   uint64_t out_cap;

@@ -175,7 +175,10 @@ __global__ void k_corr_cols(TraceArgs a) {
     const uint32_t orr = (inb ? brb : bra) + (r ? __popc((inb ? wrb : wra) & ((1u << r) - 1u)) : 0u);
     if (of + orr == target) {
       const uint32_t slot = atomicAdd(&a.ent_cnt[s], 1u);
-      if (slot < a.W) a.ent[s * a.W + slot] = (uint32_t)j;
+      if (slot < a.W) {
+        a.ent[s * a.W + slot] = (uint32_t)j;
+        a.cmap[s * (a.n + 1) + j] = (uint16_t)slot;  // the column -> walker map (see map_lookup)
+      }
     }
   }
 }
@@ -367,6 +370,39 @@ __device__ uint64_t walk_segment_warp(const TraceArgs& a, uint64_t hi, uint64_t 
   return j;
 }
 
+// Column -> walker map: k_corr_cols writes, for every corridor column j it gives a walker k < W, k at cmap[s][j].
+// The rest of the map is never cleared, so a lookup checks its answer: k names the walker entering at column e only
+// when k is one of the segment's walkers and that walker's entry is e (the entries of a segment are distinct).
+constexpr uint16_t kNoWalker = 0xFFFF;
+
+__device__ __forceinline__ uint16_t map_lookup(const TraceArgs& a, uint64_t s, uint32_t c, uint32_t e) {
+  const uint16_t k = a.cmap[s * (a.n + 1) + e];
+  return (k < c && a.ent[s * a.W + k] == e) ? k : kNoWalker;
+}
+
+// The link of a walker of segment s with exit x: the walker of segment s - 1 whose entry is x, or kNoWalker (none of
+// its walkers enters there: its corridor had more columns than walkers). The entries and counts of segments below
+// the last are final once the corridor pass is done, so a walker finds its link right after its own walk.
+__device__ __forceinline__ uint16_t walker_link(const TraceArgs& a, uint64_t s, uint32_t x) {
+  if (s == 0) return kNoWalker;
+  const uint32_t cntb = a.ent_cnt[s - 1], cb = cntb < a.W ? cntb : a.W;
+  if (cb > kWalkers) return map_lookup(a, s - 1, cb, x);
+  uint32_t hit = 0;  // the (at most 32) entries are loaded together, then the first equal one is taken
+#pragma unroll
+  for (uint32_t kk = 0; kk < kWalkers; ++kk)
+    if (kk < cb && a.ent[(s - 1) * a.W + kk] == x) hit |= 1u << kk;
+  return hit ? (uint16_t)(__ffs(hit) - 1) : kNoWalker;
+}
+
+// The same for a whole warp (all lanes, the same x): lane kk compares entry kk of a narrow segment below.
+__device__ __forceinline__ uint16_t walker_link_warp(const TraceArgs& a, uint64_t s, uint32_t x, uint32_t lane) {
+  if (s == 0) return kNoWalker;
+  const uint32_t cntb = a.ent_cnt[s - 1], cb = cntb < a.W ? cntb : a.W;
+  if (cb > kWalkers) return map_lookup(a, s - 1, cb, x);
+  const uint32_t b = __ballot_sync(kFull, lane < cb && a.ent[(s - 1) * a.W + lane] == x);
+  return b ? (uint16_t)(__ffs(b) - 1) : kNoWalker;
+}
+
 // Walkers of segment s. A segment whose corridor has at most gridDim.y columns (the usual case for pairs of similar
 // length) gives each walker a whole warp: block (s, k) walks from the k-th corridor column with
 // walk_segment_warp, whose lanes fetch 32 rows at a time and follow one path, so a row costs a few dependent
@@ -385,6 +421,7 @@ __global__ void k_walk(TraceArgs a) {
     const uint64_t e = last ? a.n : a.ent[s * a.W + k];
     uint32_t nc = 0;
     const uint64_t x = walk_segment_warp(a, hi, lo, e, a.chars + (s * (a.W + 1) + k) * a.H, &nc);
+    const uint16_t l = walker_link_warp(a, s, (uint32_t)x, threadIdx.x);
     if (threadIdx.x == 0) {
       if (last) {
         a.ent[s * a.W] = (uint32_t)a.n;
@@ -392,6 +429,7 @@ __global__ void k_walk(TraceArgs a) {
       }
       a.ext[s * a.W + k] = (uint32_t)x;
       a.nch[s * a.W + k] = nc;
+      a.link[s * a.W + k] = l;
     }
     return;
   }
@@ -402,90 +440,85 @@ __global__ void k_walk(TraceArgs a) {
   const uint64_t x = walk_segment(a, hi, lo, e, a.chars + (s * (a.W + 1) + k) * a.H, &nc);
   a.ext[s * a.W + k] = (uint32_t)x;
   a.nch[s * a.W + k] = nc;
+  a.link[s * a.W + k] = walker_link(a, s, (uint32_t)x);
 }
 
-// Follows the true path from (m, n) down the segments. The first 32 walkers of every segment are staged in shared
-// memory and every block thread links walker k of segment s to the walker of segment s - 1 whose entry is k's exit
-// (if any); thread 0 then follows the links, one shared load per segment. Where a link is missing (the entry is
-// among walkers past the first 32 of a wide corridor, or among none), warp 0 continues segment by segment: it
-// searches all W walkers in global memory, and when the entry is not among them (more corridor columns than W)
-// walks the segment itself.
+// Follows the true path from (m, n) down the segments: warp 0 follows the walkers' links (k_walk), the first 32 of
+// every segment staged in shared memory, from segment S - 1's walker (it starts at (m, n)); where a link is missing
+// (the entry is not among the segment's W walkers: more corridor columns than walkers) the warp walks that segment
+// itself and looks its exit up among the next segment's walkers, until the path meets a walker again.
 constexpr uint32_t kChainThreads = 256;
-constexpr uint8_t kNoLink = 0xFF;
+
+__device__ __forceinline__ bool chain_lookup(const TraceArgs& a, const uint32_t* ent32, const uint32_t* cnt,
+                                             uint64_t s, uint32_t e, uint32_t lane, uint32_t* k_out) {
+  const uint32_t c = cnt[s] < a.W ? cnt[s] : a.W;
+  if (c <= kWalkers) {
+    const bool hit = lane < c && ent32[s * kWalkers + lane] == e;
+    const uint32_t b = __ballot_sync(kFull, hit);
+    *k_out = b ? (uint32_t)__ffs(b) - 1 : 0u;
+    return b != 0;
+  }
+  const uint16_t k = map_lookup(a, s, c, e);
+  *k_out = k;
+  return k != kNoWalker;
+}
+
+// Shared memory of k_chain: ent32 [S][32] and cnt [S] (words), then link32 [S][32] (16-bit) from a 16-byte boundary.
+__host__ __device__ constexpr uint64_t chain_link_offset(uint64_t S) { return (S * kWalkers + S + 3) & ~(uint64_t)3; }
 
 __global__ void __launch_bounds__(kChainThreads) k_chain(TraceArgs a) {
   extern __shared__ uint32_t sm[];
-  uint32_t* ent = sm;                         // [S][kWalkers]
-  uint32_t* ext = sm + a.S * kWalkers;        // [S][kWalkers]
-  uint32_t* cnt = sm + 2 * a.S * kWalkers;    // [S]
-  uint8_t* link = reinterpret_cast<uint8_t*>(sm + 2 * a.S * kWalkers + a.S);  // [S][kWalkers]
-  __shared__ int32_t stop_s;
-  __shared__ uint32_t stop_e;
+  uint32_t* ent32 = sm;                   // [S][kWalkers]: the first 32 entries of every segment
+  uint32_t* cnt = sm + a.S * kWalkers;    // [S]
+  uint16_t* link32 = reinterpret_cast<uint16_t*>(sm + chain_link_offset(a.S));  // [S][kWalkers]
   const uint32_t tid = threadIdx.x, lane = tid & 31;
+  const uint32_t S = (uint32_t)a.S, W = a.W;
 #pragma unroll 8
-  for (uint64_t i = tid; i < a.S * kWalkers; i += kChainThreads) {  // the loads of 8 rounds in flight together
-    const uint64_t src = (i / kWalkers) * a.W + (i % kWalkers);
-    ent[i] = a.ent[src];
-    ext[i] = a.ext[src];
+  for (uint32_t i = tid; i < S * kWalkers; i += kChainThreads) {  // the loads of 8 rounds in flight together
+    const uint64_t src = (uint64_t)(i / kWalkers) * W + (i % kWalkers);
+    ent32[i] = a.ent[src];
+    link32[i] = a.link[src];
   }
-  for (uint64_t i = tid; i < a.S; i += kChainThreads) cnt[i] = a.ent_cnt[i];
+  for (uint32_t i = tid; i < S; i += kChainThreads) cnt[i] = a.ent_cnt[i];
+  __shared__ int32_t stop_s;
+  __shared__ uint32_t stop_k;
   __syncthreads();
-  for (uint64_t i = tid; i < a.S * kWalkers; i += kChainThreads) {
-    const uint64_t sg = i / kWalkers, k = i % kWalkers;
-    uint8_t l = kNoLink;
-    const uint32_t c = cnt[sg] < (uint32_t)kWalkers ? cnt[sg] : (uint32_t)kWalkers;
-    if (sg > 0 && k < c) {
-      const uint32_t cb = cnt[sg - 1] < (uint32_t)kWalkers ? cnt[sg - 1] : (uint32_t)kWalkers;
-      const uint32_t x = ext[i];
-      for (uint32_t kk = 0; kk < cb; ++kk)
-        if (ent[(sg - 1) * kWalkers + kk] == x) {
-          l = (uint8_t)kk;
-          break;
-        }
-    }
-    link[i] = l;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    // segment S-1's first walker starts at (m, n)
-    int64_t s = (int64_t)a.S - 1;
-    uint32_t k = 0;
+  if (tid == 0) {  // thread 0 follows the links from segment S-1's walker (it starts at (m, n)) as far as they go
+    int64_t s0 = (int64_t)a.S - 1;
+    uint32_t k0 = 0;
     stop_s = -1;
     for (;;) {
-      a.sel[s] = k;
-      if (s == 0) break;
-      const uint8_t nk = link[s * kWalkers + k];
-      if (nk == kNoLink) {
-        stop_s = (int32_t)(s - 1);
-        stop_e = ext[s * kWalkers + k];
+      a.sel[s0] = k0;
+      if (s0 == 0) break;
+      const uint16_t nk = k0 < kWalkers ? link32[s0 * kWalkers + k0] : a.link[s0 * a.W + k0];
+      if (nk == kNoWalker) {
+        stop_s = (int32_t)s0;
+        stop_k = k0;
         break;
       }
-      k = nk;
-      --s;
+      k0 = nk;
+      --s0;
     }
   }
   __syncthreads();
   if (tid >= 32 || stop_s < 0) return;
-  uint64_t e = stop_e;
-  for (int64_t s = stop_s; s >= 0; --s) {
-    const uint32_t c = cnt[s] < a.W ? cnt[s] : a.W;
-    const bool hit = lane < c && ent[s * kWalkers + lane] == (uint32_t)e;
-    uint32_t b = __ballot_sync(kFull, hit);
-    uint32_t k = b ? (uint32_t)__ffs(b) - 1 : 0u;
-    uint32_t exit_col = b ? ext[s * kWalkers + k] : 0u;
-    for (uint32_t base = kWalkers; !b && base < c; base += kWalkers) {  // a wide corridor
-      const uint32_t q = base + lane;
-      b = __ballot_sync(kFull, q < c && a.ent[(uint64_t)s * a.W + q] == (uint32_t)e);
-      if (b) {
-        k = base + (uint32_t)__ffs(b) - 1;
-        exit_col = a.ext[(uint64_t)s * a.W + k];
-      }
+  // warp 0 from the first missing link on
+  int64_t s = stop_s;
+  uint32_t k = stop_k;
+  for (;;) {
+    if (lane == 0) a.sel[s] = k;
+    if (s == 0) break;
+    const uint16_t nk = k < kWalkers ? link32[s * kWalkers + k] : a.link[s * a.W + k];
+    if (nk != kNoWalker) {
+      k = nk;
+      --s;
+      continue;
     }
-    if (b) {
-      if (lane == 0) a.sel[s] = k;
-      e = exit_col;
-    } else {
-      // the entry is not among the walkers (more corridor columns than walkers): the warp walks the segment here
+    // no walker of segment s - 1 enters at this exit: walk segments here until the path meets a walker again
+    uint64_t e = a.ext[s * a.W + k];
+    bool met = false;
+    while (!met) {
+      --s;
       const uint64_t lo = (uint64_t)s * a.H, hi = ((uint64_t)s + 1) * a.H < a.m ? ((uint64_t)s + 1) * a.H : a.m;
       uint32_t nc = 0;
       e = walk_segment_warp(a, hi, lo, e, a.chars + ((uint64_t)s * (a.W + 1) + a.W) * a.H, &nc);
@@ -493,7 +526,10 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(TraceArgs a) {
         a.sel[s] = a.W;
         a.ent_cnt[s] = 0x80000000u | nc;  // fallback count, read by k_finalize
       }
+      if (s == 0) return;
+      met = chain_lookup(a, ent32, cnt, (uint64_t)(s - 1), (uint32_t)e, lane, &k);
     }
+    --s;  // the walker k of segment s (now s - 1 of the walked one) continues the path
   }
 }
 
@@ -620,12 +656,12 @@ cudaError_t launch_traceback(const TraceArgs& a, cudaStream_t st) {
   // gridDim.y: enough blocks for W walkers of a thread each, and at least kWarpWalkers (a warp per walker)
   const unsigned walk_y = (unsigned)std::max<uint64_t>(a.W / kWalkers, kWarpWalkers);
   k_walk<<<dim3((unsigned)a.S, walk_y), kWalkers, 0, st>>>(a);
-  const size_t chain_smem = (size_t)(2 * a.S * kWalkers + a.S) * sizeof(uint32_t) + a.S * kWalkers;
+  const size_t chain_smem = (size_t)chain_link_offset(a.S) * sizeof(uint32_t) + a.S * kWalkers * sizeof(uint16_t);
   cudaError_t e = once_per_device_attr(
       [] {
         return cudaFuncSetAttribute(
             k_chain, cudaFuncAttributeMaxDynamicSharedMemorySize,
-            (int)((2 * kMaxSegments * kWalkers + kMaxSegments) * sizeof(uint32_t) + kMaxSegments * kWalkers));
+            (int)(chain_link_offset(kMaxSegments) * sizeof(uint32_t) + kMaxSegments * kWalkers * sizeof(uint16_t)));
       },
       chain_attr_done);
   if (e != cudaSuccess) return e;
