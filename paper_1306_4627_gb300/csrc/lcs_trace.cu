@@ -142,43 +142,67 @@ __global__ void k_corr_pre(TraceArgs a) {
 // Thread (q, boundary k): the columns j = 32q .. 32q + 31 (up to n) of the boundary's row. ones_f(j) comes from
 // the forward snapshot's word q, ones_r(n - j) from the at most two words of the reverse snapshot that hold the
 // positions n - 32q - 31 .. n - 32q, so a thread reads six words for its 32 columns.
-__global__ void k_corr_cols(TraceArgs a) {
+__global__ void __launch_bounds__(128) k_corr_cols(TraceArgs a) {
+  __shared__ uint32_t wsum[4];
+  __shared__ uint32_t base_s;
   const uint64_t k = blockIdx.y + 1;
   const uint64_t wp1 = a.w + 1;
   const uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t j0 = q * 32;
-  if (j0 > a.n) return;
-  const uint32_t* vf = a.snapF + (k - 1) * a.wpad;
-  const uint32_t* vr = a.snapR + (a.S - k - 1) * a.wpad;
-  const uint32_t* pf = a.colsum + (2 * (k - 1)) * wp1;
-  const uint32_t* pr = a.colsum + (2 * (k - 1) + 1) * wp1;
-  const uint32_t target = (uint32_t)(a.n - *a.L);  // c[i,j] + suffix = n - (ones_f + ones_r); optimal at n - L
   const uint64_t s = k - 1;
-  const uint32_t bf = pf[q], wf = vf[q];
-  const uint64_t xb = a.n - j0;                      // the reverse position of column j0 (the largest)
-  const uint64_t qb = xb >> 5;
-  const uint64_t qa = xb >= 31 ? (xb - 31) >> 5 : 0; // the word of the smallest position used
-  const uint32_t bra = pr[qa], wra = vr[qa];
-  // Over the thread's columns, ones_f(j) never falls below its value at j0 (bf) and ones_r(n - j) never below its
-  // value at the smallest reverse position used (xa): when even that sum is above the optimum, no column here is
-  // on an optimal path (the usual case: a corridor is a few columns of the row).
-  const uint32_t ra = (uint32_t)((xb >= 31 ? xb - 31 : 0) & 31);  // xa = that position, in word qa
-  if (bf + bra + (ra ? __popc(wra & ((1u << ra) - 1u)) : 0u) > target) return;
-  const uint32_t brb = pr[qb], wrb = qb < a.w ? vr[qb] : 0u;
-  for (uint32_t t = 0; t < 32; ++t) {
-    const uint64_t j = j0 + t;
-    if (j > a.n) break;
-    const uint64_t x = a.n - j;
-    const uint32_t r = (uint32_t)(x & 31);
-    const bool inb = (x >> 5) == qb;
-    const uint32_t of = bf + (t ? __popc(wf & ((1u << t) - 1u)) : 0u);
-    const uint32_t orr = (inb ? brb : bra) + (r ? __popc((inb ? wrb : wra) & ((1u << r) - 1u)) : 0u);
-    if (of + orr == target) {
-      const uint32_t slot = atomicAdd(&a.ent_cnt[s], 1u);
-      if (slot < a.W) {
-        a.ent[s * a.W + slot] = (uint32_t)j;
-        a.cmap[s * (a.n + 1) + j] = (uint16_t)slot;  // the column -> walker map (see map_lookup)
+  uint32_t hits = 0;  // bit t: column j0 + t is a corridor column
+  if (j0 <= a.n) {
+    const uint32_t* vf = a.snapF + (k - 1) * a.wpad;
+    const uint32_t* vr = a.snapR + (a.S - k - 1) * a.wpad;
+    const uint32_t* pf = a.colsum + (2 * (k - 1)) * wp1;
+    const uint32_t* pr = a.colsum + (2 * (k - 1) + 1) * wp1;
+    const uint32_t target = (uint32_t)(a.n - *a.L);  // c[i,j] + suffix = n - (ones_f + ones_r); optimal at n - L
+    const uint32_t bf = pf[q], wf = vf[q];
+    const uint64_t xb = a.n - j0;                      // the reverse position of column j0 (the largest)
+    const uint64_t qb = xb >> 5;
+    const uint64_t qa = xb >= 31 ? (xb - 31) >> 5 : 0; // the word of the smallest position used
+    const uint32_t bra = pr[qa], wra = vr[qa];
+    // Over the thread's columns, ones_f(j) never falls below its value at j0 (bf) and ones_r(n - j) never below
+    // its value at the smallest reverse position used (xa): when even that sum is above the optimum, no column here
+    // is on an optimal path (the usual case: a corridor is a few columns of the row).
+    const uint32_t ra = (uint32_t)((xb >= 31 ? xb - 31 : 0) & 31);  // xa = that position, in word qa
+    if (bf + bra + (ra ? __popc(wra & ((1u << ra) - 1u)) : 0u) <= target) {
+      const uint32_t brb = pr[qb], wrb = qb < a.w ? vr[qb] : 0u;
+      for (uint32_t t = 0; t < 32; ++t) {
+        const uint64_t j = j0 + t;
+        if (j > a.n) break;
+        const uint64_t x = a.n - j;
+        const uint32_t r = (uint32_t)(x & 31);
+        const bool inb = (x >> 5) == qb;
+        const uint32_t of = bf + (t ? __popc(wf & ((1u << t) - 1u)) : 0u);
+        const uint32_t orr = (inb ? brb : bra) + (r ? __popc((inb ? wrb : wra) & ((1u << r) - 1u)) : 0u);
+        if (of + orr == target) hits |= 1u << t;
       }
+    }
+  }
+  // Walker slots in column order within the block: a scan of the threads' counts, one reservation per block, so
+  // that the walkers of a warp start at neighbouring corridor columns (their paths run together).
+  const uint32_t cnt = __popc(hits), lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t incl = cnt;
+#pragma unroll
+  for (uint32_t off = 1; off < 32; off <<= 1) {
+    const uint32_t o = __shfl_up_sync(kFull, incl, off);
+    if (lane >= off) incl += o;
+  }
+  if (lane == 31) wsum[wid] = incl;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint32_t total = wsum[0] + wsum[1] + wsum[2] + wsum[3];
+    base_s = total ? atomicAdd(&a.ent_cnt[s], total) : 0u;
+  }
+  __syncthreads();
+  uint32_t slot = base_s + incl - cnt;
+  for (uint32_t w = 0; w < wid; ++w) slot += wsum[w];
+  for (uint32_t h = hits; h; h &= h - 1, ++slot) {
+    const uint64_t j = j0 + (uint32_t)(__ffs(h) - 1);
+    if (slot < a.W) {
+      a.ent[s * a.W + slot] = (uint32_t)j;
+      a.cmap[s * (a.n + 1) + j] = (uint16_t)slot;  // the column -> walker map (see map_lookup)
     }
   }
 }
@@ -200,68 +224,81 @@ __device__ __forceinline__ uint32_t p_word(const TraceArgs& a, uint32_t code, in
 }
 
 // Walks rows hi..lo+1 from column e; returns the exit column (at row lo); writes emitted symbols to out_chars.
-// The rows are taken 16 at a time: the bitmap and match-mask words of the group's rows at the walk's current
-// 32-column word are requested together (the walk usually stays in one word for many rows), with the symbol codes
-// of the next group, so the loads of a group overlap; a row whose scan leaves that word reads its words directly.
+// Requires hi a multiple of B and hi - lo a multiple of kWalkGroup (every segment but the last: H is a multiple of
+// 32 B). The rows are taken in aligned groups of kWalkGroup: the bitmap words of a group's rows at one 32-column
+// word lie at fixed offsets from one address (the fill's layout below), so the group's bitmap and match-mask words
+// at the walk's current word are requested together, with one address computation; the symbol codes and symbols of
+// the next group (code in bits 0-7, symbol in bits 8-15) are requested a group ahead. When the walk moves to
+// another word inside the group (a diagonal step across the word's edge, or a LEFT run past it), the group's
+// remaining rows are requested again at that word.
+constexpr int kWalkGroup = 16;
+
+template <int B>
 __device__ uint64_t walk_segment(const TraceArgs& a, uint64_t hi, uint64_t lo, uint64_t e, uint8_t* out_chars,
                                  uint32_t* out_cnt) {
-  constexpr int kG = 16;
+  constexpr int kG = kWalkGroup;
+  constexpr uint32_t lb = B == 8 ? 3 : 4;
+  static_assert(B == 8 || B == 16, "rows per step");
   uint64_t i = hi, j = e;
   uint32_t cnt = 0;
-  uint32_t cd[kG];  // symbol codes of the group's rows, requested one group ahead (they do not depend on the walk)
+  const uint64_t wp = a.wpad;
+  uint32_t cd[kG];  // code | symbol << 8 of the group's rows
 #pragma unroll
-  for (int k = 0; k < kG; ++k) cd[k] = i > lo + (uint64_t)k ? a.xcode[i - k - 1] : 0u;
+  for (int k = 0; k < kG; ++k)
+    cd[k] = i > lo + (uint64_t)k ? (uint32_t)a.xcode[i - k - 1] | (uint32_t)a.x[i - k - 1] << 8 : 0u;
   while (i > lo && j > 0) {
-    const int64_t Qg = (int64_t)(j >> 5);
-    uint32_t dv[kG], pa[kG], pb[kG], ncd[kG];
+    uint32_t ncd[kG];
+    const bool more = i > lo + kG;
 #pragma unroll
-    for (int k = 0; k < kG; ++k) {
-      const bool ok = i > lo + (uint64_t)k;
-      dv[k] = ok ? t_word(a, i - k, (uint64_t)Qg) : 0u;
-      pa[k] = ok ? p_word(a, cd[k], Qg) : 0u;
-      pb[k] = ok ? p_word(a, cd[k], Qg - 1) : 0u;
-    }
+    for (int k = 0; k < kG; ++k)
+      ncd[k] = more ? (uint32_t)a.xcode[i - kG - k - 1] | (uint32_t)a.x[i - kG - k - 1] << 8 : 0u;
+    const uint64_t rb0 = (i >> lb) - 1;  // the row-block of the group's first row, i - 1
+    uint32_t done = 0;                   // rows of the group walked
+    for (;;) {
+      const uint64_t Qg = j >> 5;
+      // t_word(i - k, Qg) = tp[off(k)]: row i - 1 - k is row B - 1 - k % B of row-block rb0 - k / B
+      const uint32_t* tp = a.T + ((((Qg >> 5) * (a.R + 31) + rb0 + (Qg & 31)) << (5 + lb)) + (Qg & 31) * 4);
+      const uint32_t* pp = a.peq + Qg;
+      const uint32_t border = Qg ? kFull : ~1u;  // column 0 is the border
+      uint32_t pm[kG], ev[kG];  // bit b: a match at column 32 Qg + b; a match or an UP cell there
 #pragma unroll
-    for (int k = 0; k < kG; ++k) {  // the next group (a group ends early only when the walk ends)
-      const bool ok = i > lo + (uint64_t)(kG + k);
-      ncd[k] = ok ? a.xcode[i - kG - k - 1] : 0u;
-    }
+      for (int k = 0; k < kG; ++k) {
+        const int bk = B - 1 - (k % B);
+        const int off = -((k / B) << (5 + lb)) + (bk >> 2) * 128 + (bk & 3);
+        const uint32_t d = tp[off];
+        const uint32_t* pr = pp + (uint64_t)(cd[k] & 0xFFu) * wp;
+        const uint32_t pa = __ldg(pr), pb = Qg ? __ldg(pr - 1) : 0u;
+        pm[k] = (pa << 1) | (pb >> 31);
+        ev[k] = (pm[k] | ~d) & border;
+      }
+      bool again = false;  // the walk moved to another word: request the remaining rows there
 #pragma unroll
-    for (int k = 0; k < kG; ++k) {
-      if (i <= lo || j == 0) break;
-      const uint32_t code = cd[k];
-      int64_t Q = (int64_t)(j >> 5);
-      uint32_t mask = kFull >> (31 - (uint32_t)(j & 31));
-      uint32_t pm = 0, stop = 0;
-      for (;;) {
-        uint32_t d;
-        if (Q == Qg) {
-          d = dv[k];
-          pm = (pa[k] << 1) | (pb[k] >> 31);
-        } else {
-          d = t_word(a, i, (uint64_t)Q);
-          pm = (p_word(a, code, Q) << 1) | (p_word(a, code, Q - 1) >> 31);
+      for (int k = 0; k < kG; ++k) {
+        if (k < (int)done) continue;
+        const uint32_t stop = ev[k] & (kFull >> (31u - (uint32_t)(j & 31)));  // columns 32 Qg .. j
+        if (!stop) {  // a LEFT run past the word's first column: this row's scan goes on in the previous word
+          if (Qg == 0) {
+            j = 0;
+          } else {
+            j = (Qg << 5) - 1;
+            again = true;
+          }
+          break;
         }
-        stop = (pm | ~d) & mask;
-        if (Q == 0) stop &= ~1u;  // column 0 is the border
-        if (stop || Q == 0) break;
-        --Q;
-        mask = kFull;
+        const uint32_t bit = 31u - __clz(stop);
+        const uint32_t mt = (pm[k] >> bit) & 1u;  // a match at column c: DIAG; else an UP cell: the walk goes up at c
+        if (mt) out_chars[cnt++] = (uint8_t)(cd[k] >> 8);
+        j = (Qg << 5) + bit - mt;
+        done = (uint32_t)k + 1;
+        if (j == 0) break;
+        if ((j >> 5) != Qg) {
+          again = true;
+          break;
+        }
       }
-      if (!stop) {
-        j = 0;
-        break;
-      }
-      const uint32_t bit = 31u - __clz(stop);
-      const uint64_t c = ((uint64_t)Q << 5) + bit;
-      if ((pm >> bit) & 1u) {
-        out_chars[cnt++] = a.x[i - 1];
-        j = c - 1;
-      } else {
-        j = c;
-      }
-      --i;
+      if (!again || done == kG) break;
     }
+    i -= kG;
 #pragma unroll
     for (int k = 0; k < kG; ++k) cd[k] = ncd[k];
   }
@@ -407,8 +444,9 @@ __device__ __forceinline__ uint16_t walker_link_warp(const TraceArgs& a, uint64_
 // length) gives each walker a whole warp: block (s, k) walks from the k-th corridor column with
 // walk_segment_warp, whose lanes fetch 32 rows at a time and follow one path, so a row costs a few dependent
 // instructions and no divergence. A wider corridor (tall pairs, hundreds of columns) runs one walker per thread:
-// block (s, y), thread t walks from column y * 32 + t. The last segment has one walker, from (m, n); it records
-// that entry for the chain pass.
+// block (s, y), thread t walks from column y * 32 + t (such a segment is never the last, so its rows hi..lo+1 are
+// aligned as walk_segment requires). The last segment has one walker, from (m, n); it records that entry for the
+// chain pass.
 __global__ void k_walk(TraceArgs a) {
   const uint64_t s = blockIdx.x;
   const bool last = s + 1 == a.S;
@@ -437,7 +475,8 @@ __global__ void k_walk(TraceArgs a) {
   if (k >= cnt) return;
   const uint64_t e = a.ent[s * a.W + k];
   uint32_t nc = 0;
-  const uint64_t x = walk_segment(a, hi, lo, e, a.chars + (s * (a.W + 1) + k) * a.H, &nc);
+  uint8_t* out = a.chars + (s * (a.W + 1) + k) * a.H;
+  const uint64_t x = a.B == 8 ? walk_segment<8>(a, hi, lo, e, out, &nc) : walk_segment<16>(a, hi, lo, e, out, &nc);
   a.ext[s * a.W + k] = (uint32_t)x;
   a.nch[s * a.W + k] = nc;
   a.link[s * a.W + k] = walker_link(a, s, (uint32_t)x);
