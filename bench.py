@@ -287,11 +287,15 @@ def measure_probes(device: int) -> dict:
              (("row_update", 0), ("row_update_traceback", 1), ("lop3", 2))}
     floors = {f"rows{b}_{'traceback' if tb else 'length'}": lcs.probe_step_floor(device, b, tb, 8192)
               for b in (8, 16) for tb in (False, True)}
+    mask_src = {name: lcs.probe_step_masks(device, k, 8192) for k, name in enumerate(lcs.MASK_SOURCES)}
     clocks = sampler.stop()
-    return {"int_rate": rates, "step_floor_cycles": floors, "clocks": clocks,
+    return {"int_rate": rates, "step_floor_cycles": floors, "step_mask_source_cycles": mask_src, "clocks": clocks,
             "note": "int_rate: every SM full of independent chains of the mix (ops = instructions of the mix); "
                     "step_floor_cycles: one warp per SM sub-partition running only the fill's row arithmetic and "
-                    "carry shuffles (plus its two bitmap stores per step in traceback mode), masks in registers"}
+                    "carry shuffles (plus its two bitmap stores per step in traceback mode), masks in registers; "
+                    "step_mask_source_cycles: the 8-row traceback step with its masks from registers, from the "
+                    "fill's shared table, or formed from two bit planes of Y's codes (byte-permuted or expanded "
+                    "row codes)"}
 
 
 def alu_line(cells: int, ops_per_word: int, kernel_ms: float, clocks: dict, kernel: str, probes: dict | None,

@@ -138,6 +138,19 @@ LCS_API int lcs_probe_int_rate(int device, uint32_t mix, uint32_t iters, lcs_int
 LCS_API int lcs_probe_step_floor(int device, uint32_t rows_per_step, int traceback, uint32_t steps,
                                  double* cycles_per_step);
 
+/* The same 8-row traceback step with its match masks supplied four ways (alphabet of 4 symbols, so Y's codes have
+ * two bit planes), to weigh the fill's shared-memory table against masks formed in registers:
+ * source 0: the masks in registers (= lcs_probe_step_floor(device, 8, 1, ...));
+ * source 1: the fill's way: each row's mask read from a shared table of every symbol's mask at the lane's word, at
+ *           the row's symbol offset (offsets from a shared ring two steps ahead, masks one step ahead);
+ * source 2: P = ~((pl0 ^ s0) | (pl1 ^ s1)) from the lane's two bit planes pl0, pl1 of Y's codes, s0 / s1 all ones
+ *           where the row's code bit is set, each made by one byte permute from codes stored as byte sign bits (one
+ *           16-byte shared load per step);
+ * source 3: the same formula with s0 / s1 of every row stored expanded (four 16-byte shared loads per step).
+ * steps (1 .. 2^24); *cycles_per_step is the median of the 4 warps. Blocking.
+ * Errors: LCS_ERR_INVALID (source > 3, steps out of range, NULL output, no such device), LCS_ERR_CUDA. */
+LCS_API int lcs_probe_step_masks(int device, uint32_t source, uint32_t steps, double* cycles_per_step);
+
 /* ---- length (paper §I.C, LCS-length; returns c[m,n]) --------------------------------------------------------- */
 
 /* Host buffers x[0..m), y[0..n); writes c[m,n] to *out_len. Blocking. m = 0 or n = 0 gives 0. Errors:

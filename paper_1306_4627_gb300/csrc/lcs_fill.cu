@@ -528,25 +528,112 @@ cudaError_t launch_t(const FillArgs& a, cudaStream_t st) {
 // ---- step floor probe --------------------------------------------------------------------------------------------
 // The fill's step without the work around it: one block of 4 warps (one per SM sub-partition, as in the fill) runs
 // `steps` systolic steps of B rows with exactly the fill's row arithmetic (rows<B, TB>: the row updates and the two
-// carry shuffles per step), the match masks held in registers, and in traceback mode the fill's two 16-byte bitmap
-// stores per lane and step (into a 64-step ring per warp that stays in L2). Each warp times its steps with clock64
-// after 64 untimed ones. Index ranges: masks[0..64), cycles[0..4), sink[0..128),
-// tbuf[0 .. 4 warps * 64 slots * 32 lanes * B words) with B <= 16.
-template <int B, bool TB>
+// carry shuffles per step) and in traceback mode the fill's two 16-byte bitmap stores per lane and step (into a
+// 64-step ring per warp that stays in L2). Each warp times its steps with clock64 after 64 untimed ones.
+// MSRC chooses where the rows' match masks come from (lane l works on row-block r = t - l at step t, as in the
+// fill; the alphabet has 4 symbols, so Y's codes have two bit planes):
+//   kMaskRegs   the masks held in registers (the floor of the row arithmetic);
+//   kMaskTable  the fill's way: a shared table of every symbol's mask at the lane's word, read at the row's symbol
+//               offset; the B offsets of a row-block come from a shared ring two steps ahead (two 16-byte loads), the
+//               masks one step ahead (B loads);
+//   kMaskPrmt   formed in registers from the lane's two bit planes of Y's codes: P = ~((pl0 ^ s0) | (pl1 ^ s1)),
+//               s0 / s1 all ones where the row's code bit is set, each taken from the sign bit of a byte by one
+//               byte permute; the codes of a row-block (bit b of row k at the top of byte k % 4 of word 2b + k / 4)
+//               come from a shared ring one step ahead (one 16-byte load);
+//   kMaskRows   the same formula with s0 / s1 of every row stored expanded in the ring (four 16-byte loads).
+// Index ranges: masks[0..64), cycles[0..4), sink[0..128), tbuf[0 .. 4 warps * 64 slots * 32 lanes * B words) with
+// B <= 16; the shared table [4 warps][8 rows][32 lanes] and ring [4 warps][4 vectors][64 slots] (B = 8 when MSRC
+// is not kMaskRegs).
+enum { kMaskRegs = 0, kMaskTable = 1, kMaskPrmt = 2, kMaskRows = 3 };
+
+__device__ __forceinline__ uint32_t probe_code(const uint32_t* masks, uint32_t slot, uint32_t k) {
+  return (masks[(slot + 7 * k) & 63] >> (k + slot % 7)) & 3u;  // the code (0..3) of row k of ring slot `slot`
+}
+
+template <int B, bool TB, int MSRC>
 __global__ void __launch_bounds__(kFillThreads, 1)
     k_step_floor(const uint32_t* masks, uint32_t steps, unsigned long long* cycles, uint32_t* sink, uint4* tbuf) {
+  static_assert(MSRC == kMaskRegs || B == 8, "mask sources other than registers are probed with 8 rows per step");
+  __shared__ uint32_t tab_s[kFillWarps][8][32];
+  __shared__ uint4 ring_s[kFillWarps][4][64];
   const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  uint32_t P[B];
+  const uint32_t pl0 = masks[lane], pl1 = masks[lane + 32];  // the lane's two bit planes of Y's codes
+  if (MSRC != kMaskRegs) {
+    for (uint32_t c = 0; c < 8; ++c)  // the mask of code c at the lane's word (rows 4..7: no symbol, zero)
+      tab_s[wib][c][lane] = c < 4 ? ~((pl0 ^ (0u - (c & 1u))) | (pl1 ^ (0u - (c >> 1)))) : 0u;
+    for (uint32_t sl = lane; sl < 64; sl += 32) {
+      uint32_t cd[8];
+#pragma unroll
+      for (uint32_t k = 0; k < 8; ++k) cd[k] = probe_code(masks, sl, k);
+      if (MSRC == kMaskTable) {
+        ring_s[wib][0][sl] = make_uint4(cd[0] * 32, cd[1] * 32, cd[2] * 32, cd[3] * 32);
+        ring_s[wib][1][sl] = make_uint4(cd[4] * 32, cd[5] * 32, cd[6] * 32, cd[7] * 32);
+      } else if (MSRC == kMaskPrmt) {
+        uint32_t w[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (uint32_t k = 0; k < 8; ++k)
+#pragma unroll
+          for (uint32_t b = 0; b < 2; ++b) w[2 * b + k / 4] |= ((cd[k] >> b) & 1u) << (8 * (k % 4) + 7);
+        ring_s[wib][0][sl] = make_uint4(w[0], w[1], w[2], w[3]);
+      } else {
+        uint32_t e[16];
+#pragma unroll
+        for (uint32_t k = 0; k < 8; ++k) {
+          e[k] = 0u - (cd[k] & 1u);
+          e[8 + k] = 0u - (cd[k] >> 1);
+        }
+#pragma unroll
+        for (uint32_t v = 0; v < 4; ++v) ring_s[wib][v][sl] = make_uint4(e[4 * v], e[4 * v + 1], e[4 * v + 2], e[4 * v + 3]);
+      }
+    }
+  }
+  __syncthreads();
+  uint32_t P[B];  // kMaskRegs: the masks; kMaskTable: the next step's masks
 #pragma unroll
   for (int b = 0; b < B; ++b) P[b] = masks[(threadIdx.x * B + b) & 63];
+  uint32_t xo[B];  // kMaskTable: symbol offsets of the row-block two steps ahead
+#pragma unroll
+  for (int b = 0; b < B; ++b) xo[b] = 0;
+  uint4 c4[4] = {};  // kMaskPrmt / kMaskRows: the codes of the next step's row-block
+  const uint32_t* tp_s = &tab_s[wib][0][lane];
   uint32_t V = kFull, cin_a = 0, cin_b = 0, acc = 0;
   uint4* tp = tbuf + (size_t)wib * 64 * 32 * (B / 4) + lane;  // the fill's chunk layout: [B/4][32 lanes] vectors
   long long t0 = 0;
 #pragma unroll 1
   for (uint32_t t = 0; t < steps + 64; ++t) {
     if (t == 64) t0 = clock64();
+    const uint32_t r = t - lane;
+    uint32_t Pu[B];
+    if (MSRC == kMaskRegs) {
+#pragma unroll
+      for (int b = 0; b < B; ++b) Pu[b] = P[b];
+    } else if (MSRC == kMaskTable) {
+#pragma unroll
+      for (int b = 0; b < B; ++b) Pu[b] = P[b];
+#pragma unroll
+      for (int b = 0; b < B; ++b) P[b] = tp_s[xo[b]];
+      const uint4 q0 = ring_s[wib][0][(r + 2) & 63], q1 = ring_s[wib][1][(r + 2) & 63];
+      xo[0] = q0.x; xo[1] = q0.y; xo[2] = q0.z; xo[3] = q0.w;
+      xo[4] = q1.x; xo[5] = q1.y; xo[6] = q1.z; xo[7] = q1.w;
+    } else if (MSRC == kMaskPrmt) {
+      const uint32_t w[4] = {c4[0].x, c4[0].y, c4[0].z, c4[0].w};
+#pragma unroll
+      for (int k = 0; k < B; ++k) {
+        const uint32_t sel = 0x8888u + 0x1111u * (uint32_t)(k % 4);  // byte k % 4, its sign bit replicated
+        const uint32_t s0 = __byte_perm(w[k / 4], 0u, sel), s1 = __byte_perm(w[2 + k / 4], 0u, sel);
+        Pu[k] = ~((pl0 ^ s0) | (pl1 ^ s1));
+      }
+      c4[0] = ring_s[wib][0][(r + 1) & 63];
+    } else {
+      const uint32_t e[16] = {c4[0].x, c4[0].y, c4[0].z, c4[0].w, c4[1].x, c4[1].y, c4[1].z, c4[1].w,
+                              c4[2].x, c4[2].y, c4[2].z, c4[2].w, c4[3].x, c4[3].y, c4[3].z, c4[3].w};
+#pragma unroll
+      for (int k = 0; k < B; ++k) Pu[k] = ~((pl0 ^ e[k]) | (pl1 ^ e[8 + k]));
+#pragma unroll
+      for (int v = 0; v < 4; ++v) c4[v] = ring_s[wib][v][(r + 1) & 63];
+    }
     uint32_t co, tw[B];
-    rows<B, TB>(P, V, cin_a, cin_b, co, cin_a, cin_b, tw);
+    rows<B, TB>(Pu, V, cin_a, cin_b, co, cin_a, cin_b, tw);
     acc += co;
     if (TB) {
       uint4* q = tp + (size_t)(t & 63) * 32 * (B / 4);
@@ -559,7 +646,7 @@ __global__ void __launch_bounds__(kFillThreads, 1)
   sink[threadIdx.x] = V ^ acc;
 }
 
-template <int B, bool TB>
+template <int B, bool TB, int MSRC = kMaskRegs>
 cudaError_t step_floor_t(uint32_t steps, double* cycles_per_step) {
   uint32_t *masks = nullptr, *sink = nullptr;
   unsigned long long* cyc = nullptr;
@@ -582,7 +669,7 @@ cudaError_t step_floor_t(uint32_t steps, double* cycles_per_step) {
     e = cudaMemcpy(masks, h, sizeof(h), cudaMemcpyHostToDevice);
   }
   if (e == cudaSuccess) {
-    k_step_floor<B, TB><<<1, kFillThreads>>>(masks, steps, cyc, sink, tbuf);
+    k_step_floor<B, TB, MSRC><<<1, kFillThreads>>>(masks, steps, cyc, sink, tbuf);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -636,6 +723,16 @@ cudaError_t step_floor(uint32_t B, bool traceback, uint32_t steps, double* cycle
   if (B == 8) return traceback ? step_floor_t<8, true>(steps, cycles_per_step) : step_floor_t<8, false>(steps, cycles_per_step);
   if (B == 16) return traceback ? step_floor_t<16, true>(steps, cycles_per_step) : step_floor_t<16, false>(steps, cycles_per_step);
   return cudaErrorInvalidValue;
+}
+
+cudaError_t step_masks(uint32_t source, uint32_t steps, double* cycles_per_step) {
+  switch (source) {
+    case kMaskRegs: return step_floor_t<8, true, kMaskRegs>(steps, cycles_per_step);
+    case kMaskTable: return step_floor_t<8, true, kMaskTable>(steps, cycles_per_step);
+    case kMaskPrmt: return step_floor_t<8, true, kMaskPrmt>(steps, cycles_per_step);
+    case kMaskRows: return step_floor_t<8, true, kMaskRows>(steps, cycles_per_step);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace lcs

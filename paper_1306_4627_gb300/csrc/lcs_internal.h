@@ -142,6 +142,9 @@ size_t fill_smem_bytes();
 // step floor probe: clock cycles of one systolic step of B rows (8 or 16) with the fill's row arithmetic and carry
 // shuffles only (masks in registers; the two bitmap stores per step in traceback mode), one warp per scheduler
 cudaError_t step_floor(uint32_t B, bool traceback, uint32_t steps, double* cycles_per_step);
+// One 8-row traceback step with the match masks from source 0..3 (registers, the fill's shared table, bit planes
+// with byte-permuted codes, bit planes with expanded row masks); see k_step_floor.
+cudaError_t step_masks(uint32_t source, uint32_t steps, double* cycles_per_step);
 // length meet-in-the-middle combine: L = n - min_j (pf(j) + pr(n-j))
 cudaError_t launch_combine(const uint32_t* vf, const uint32_t* vr, uint64_t n, uint64_t w,
                            uint32_t* colsum, unsigned long long* out_len, cudaStream_t st);

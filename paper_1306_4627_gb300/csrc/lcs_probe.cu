@@ -8,6 +8,8 @@
 //     holds as many blocks as fit, so nothing but the integer pipes bounds the rate. It is the ALU roofline of the
 //     fill: the most row updates per second this GPU can execute.
 //   * lcs_probe_step_floor (lcs_fill.cu): the dependency floor of one systolic step of the fill.
+//   * lcs_probe_step_masks (lcs_fill.cu): the same step with its match masks from the fill's shared table or formed
+//     in registers from bit planes of Y's codes, to weigh the two ways of supplying them.
 #include <algorithm>
 #include <vector>
 
@@ -159,6 +161,25 @@ extern "C" int lcs_probe_step_floor(int device, uint32_t rows_per_step, int trac
     return LCS_ERR_CUDA;
   }
   const cudaError_t e = lcs::step_floor(rows_per_step, traceback != 0, steps, cycles_per_step);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return LCS_ERR_CUDA;
+  }
+  return LCS_OK;
+}
+
+extern "C" int lcs_probe_step_masks(int device, uint32_t source, uint32_t steps, double* cycles_per_step) {
+  if (!cycles_per_step || source > 3 || steps == 0 || steps > (1u << 24)) return LCS_ERR_INVALID;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return LCS_ERR_INVALID;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    return LCS_ERR_CUDA;
+  }
+  const cudaError_t e = lcs::step_masks(source, steps, cycles_per_step);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return LCS_ERR_CUDA;

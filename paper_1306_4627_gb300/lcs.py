@@ -26,7 +26,7 @@ EXPORTS = (
     "lcs_serve_poll", "lcs_serve_wait", "lcs_result_release", "lcs_serve_destroy", "lcs_ctx_set_profiling",
     "lcs_ctx_last_profile", "lcs_tables", "lcs_tables_dev", "lcs_ctx_get_fill_config", "lcs_ctx_set_fill_config",
     "lcs_ctx_autotune_dev", "lcs_ctx_get_batch_config", "lcs_ctx_set_batch_config", "lcs_ctx_autotune_batch_dev",
-    "lcs_probe_int_rate", "lcs_probe_step_floor",
+    "lcs_probe_int_rate", "lcs_probe_step_floor", "lcs_probe_step_masks",
 )
 
 
@@ -104,6 +104,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                                        ctypes.POINTER(ctypes.c_double)]),
         "lcs_probe_int_rate": (ctypes.c_int, [ctypes.c_int, u32, u32, ctypes.POINTER(IntRate)]),
         "lcs_probe_step_floor": (ctypes.c_int, [ctypes.c_int, u32, ctypes.c_int, u32, ctypes.POINTER(ctypes.c_double)]),
+        "lcs_probe_step_masks": (ctypes.c_int, [ctypes.c_int, u32, u32, ctypes.POINTER(ctypes.c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -143,6 +144,17 @@ def probe_step_floor(device: int = 0, rows_per_step: int = 8, traceback: bool = 
     c = ctypes.c_double(0.0)
     _check(_lib.lcs_probe_step_floor(device, rows_per_step, 1 if traceback else 0, steps, ctypes.byref(c)),
            "lcs_probe_step_floor")
+    return c.value
+
+
+MASK_SOURCES = ("registers", "shared_table", "planes_prmt", "planes_expanded")
+
+
+def probe_step_masks(device: int = 0, source: int = 0, steps: int = 4096) -> float:
+    """Clock cycles of one 8-row traceback fill step with its match masks from `source` (0..3, MASK_SOURCES)
+    (lcs_probe_step_masks)."""
+    c = ctypes.c_double(0.0)
+    _check(_lib.lcs_probe_step_masks(device, source, steps, ctypes.byref(c)), "lcs_probe_step_masks")
     return c.value
 
 

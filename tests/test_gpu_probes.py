@@ -28,3 +28,15 @@ def test_step_floor_plausible():
             assert 3 * b < c < 100 * b, (b, tb, c)
     with pytest.raises(lcs.LCSError):
         lcs.probe_step_floor(0, 12, False, 100)
+
+
+def test_step_mask_sources_plausible():
+    from paper_1306_4627_gb300 import lcs
+    cyc = [lcs.probe_step_masks(0, k, 2048) for k in range(len(lcs.MASK_SOURCES))]
+    for c in cyc:
+        assert 3 * 8 < c < 100 * 8, cyc
+    # source 0 is the traceback step floor itself, measured the same way
+    floor = lcs.probe_step_floor(0, 8, True, 2048)
+    assert abs(cyc[0] - floor) < 0.25 * floor, (cyc, floor)
+    with pytest.raises(lcs.LCSError):
+        lcs.probe_step_masks(0, 4, 100)
