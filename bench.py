@@ -681,17 +681,27 @@ def measure_batch(args, dev, probes=None, min_s=1.0, ws=1, rank=0, dist=None) ->
     tuned = None
     if not args.no_autotune:  # the library's batch autotuner picks words per lane, job height and blocks per SM
         tuned = ctx.autotune_batch_dev(dxs, dxo, dys, dyo, len(pairs), outd, stream=stream)
+    # the timed call takes the offsets from host memory, where the caller built them (lcs_batch_dev_hoff); the
+    # variant with device offsets (lcs_batch_dev) copies them back and waits before planning, timed beside it
+    xo_h, yo_h = xo.astype(np.uint64), yo.astype(np.uint64)
     for _ in range(args.warmup):
-        ctx.batch_dev(dxs, dxo, dys, dyo, len(pairs), outd, stream=stream)
+        ctx.batch_dev_hoff(dxs, xo_h, dys, yo_h, len(pairs), outd, stream=stream)
     ctx.sync()
     if dist is not None:
         dist.barrier()
     sampler = ClockSampler(dev.index).start()
     time.sleep(0.3)
-    tot = timed_calls(lambda: ctx.batch_dev(dxs, dxo, dys, dyo, len(pairs), outd, stream=stream), stream, min_s,
-                      flush=lambda: flush_l2(flush))
+    tot = timed_calls(lambda: ctx.batch_dev_hoff(dxs, xo_h, dys, yo_h, len(pairs), outd, stream=stream), stream,
+                      min_s, flush=lambda: flush_l2(flush))
     clocks = sampler.stop()
     ctx.sync()
+    lens_h = outd.cpu().numpy().copy()
+    outd.zero_()
+    tot_doff = timed_calls(lambda: ctx.batch_dev(dxs, dxo, dys, dyo, len(pairs), outd, stream=stream), stream,
+                           min(min_s, 0.3), flush=lambda: flush_l2(flush))
+    ctx.sync()
+    assert np.array_equal(outd.cpu().numpy(), lens_h), "the two batch entry points disagree"
+    dof_ms = max_over_ranks(float(np.median(tot_doff)), dist, dev)
     # stage split with the context's stage events (direct launches)
     ctx.set_profiling(True)
     kern, prep = [], []
@@ -746,6 +756,10 @@ def measure_batch(args, dev, probes=None, min_s=1.0, ws=1, rank=0, dist=None) ->
         "timed_s": float(np.sum(tot)) * 1e-3, "cells": total_cells, "pairs": len(all_pairs),
         "parallelism": f"pairs split over {ws} ranks, cells balanced" if ws > 1 else "1 GPU",
         "l2": "explicit 256 MiB L2 flush before every timed call (outside the events)",
+        "api": "lcs_batch_dev_hoff (strings and lengths in device memory, offsets in host memory)",
+        "device_offsets": {"api": "lcs_batch_dev (offsets in device memory: copied back, stream waited on, then "
+                                  "planned)", "ms_per_call": dof_ms,
+                           "value": total_cells / (dof_ms * 1e-3) / 1e9, "calls_timed": len(tot_doff)},
         "batch_config": tuned or None,
         "stages_ms": {"prep": float(np.median(prep)), "batch_kernel": k_ms},
         "kernel_gcups": total_cells / (k_ms * 1e-3) / 1e9,
@@ -780,8 +794,8 @@ def run_batch_workload(args):
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": r["workload"], "cells": r["cells"], "pairs": r["pairs"], "parallelism": r["parallelism"],
                    "l2": r["l2"]},
-        **{k: r[k] for k in ("batch_config", "stages_ms", "kernel_gcups", "roofline", "sequential_per_pair", "e2e",
-                              "cpu_baseline", "gpu_launches", "clocks")},
+        **{k: r[k] for k in ("api", "device_offsets", "batch_config", "stages_ms", "kernel_gcups", "roofline",
+                              "sequential_per_pair", "e2e", "cpu_baseline", "gpu_launches", "clocks")},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

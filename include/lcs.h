@@ -221,9 +221,17 @@ LCS_API int lcs_tables_dev(lcs_ctx* ctx, const uint8_t* d_x, uint64_t m, const u
 LCS_API int lcs_batch(lcs_ctx* ctx, const uint8_t* xs, const uint64_t* x_off, const uint8_t* ys, const uint64_t* y_off,
               uint64_t count, uint64_t* out_lens);
 
-/* The same with device buffers (offsets too); asynchronous in `stream`. */
+/* The same with device buffers (offsets too); asynchronous in `stream`. The batch is planned on the host, so the
+ * call copies the offsets back and waits for `stream` to reach that copy before it enqueues the batch. */
 LCS_API int lcs_batch_dev(lcs_ctx* ctx, const uint8_t* d_xs, const uint64_t* d_x_off, const uint8_t* d_ys,
                   const uint64_t* d_y_off, uint64_t count, uint64_t* d_out_lens, void* stream);
+
+/* The same with the strings and lengths in device memory and the offsets x_off / y_off (count+1 each) in host
+ * memory, as a caller that assembled the batch holds them: no copy back and no wait; the call returns once the
+ * batch is enqueued in `stream` (the offsets are read before it returns). Errors as lcs_batch, except that a
+ * device-side timeout is latched and reported by lcs_ctx_sync, as for the other asynchronous calls. */
+LCS_API int lcs_batch_dev_hoff(lcs_ctx* ctx, const uint8_t* d_xs, const uint64_t* x_off, const uint8_t* d_ys,
+                               const uint64_t* y_off, uint64_t count, uint64_t* d_out_lens, void* stream);
 
 /* Batch configuration (no counterpart in the paper: how the batched fill of §I.C is laid out on the GPU). The rows
  * of a pair are worked by a group of lanes of one warp, each lane holding consecutive 32-column words of the row.

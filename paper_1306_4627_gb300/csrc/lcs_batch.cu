@@ -838,6 +838,31 @@ extern "C" int lcs_batch_dev(lcs_ctx* c, const uint8_t* d_xs, const uint64_t* d_
   }
 }
 
+// Device strings and lengths, host offsets: the plan is made from offsets the caller already holds, so nothing is
+// copied back and the stream is not waited on; the call returns once the batch is enqueued.
+static int lcs_batch_dev_hoff_impl(lcs_ctx* c, const uint8_t* d_xs, const uint64_t* x_off, const uint8_t* d_ys,
+                                   const uint64_t* y_off, uint64_t count, uint64_t* d_out_lens, void* stream) {
+  if (!c || (count && (!x_off || !y_off || !d_out_lens))) return LCS_ERR_INVALID;
+  if (count == 0) return LCS_OK;
+  if (!offsets_ok(x_off, count) || !offsets_ok(y_off, count)) return LCS_ERR_INVALID;
+  if ((x_off[count] > x_off[0] && !d_xs) || (y_off[count] > y_off[0] && !d_ys)) return LCS_ERR_INVALID;
+  std::lock_guard<std::mutex> g(c->mu);
+  cudaSetDevice(c->device);
+  cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
+  return run_batch(c, d_xs + x_off[0], d_ys + y_off[0], x_off, y_off, count, d_out_lens, st);
+}
+
+extern "C" int lcs_batch_dev_hoff(lcs_ctx* c, const uint8_t* d_xs, const uint64_t* x_off, const uint8_t* d_ys,
+                                  const uint64_t* y_off, uint64_t count, uint64_t* d_out_lens, void* stream) {
+  try {  // no C++ exception crosses the C boundary
+    return lcs_batch_dev_hoff_impl(c, d_xs, x_off, d_ys, y_off, count, d_out_lens, stream);
+  } catch (const std::bad_alloc&) {
+    return LCS_ERR_NOMEM;
+  } catch (...) {
+    return LCS_ERR_INTERNAL;
+  }
+}
+
 static int lcs_batch_impl(lcs_ctx* c, const uint8_t* xs, const uint64_t* x_off, const uint8_t* ys,
                          const uint64_t* y_off, uint64_t count, uint64_t* out_lens) {
   if (!c || (count && (!x_off || !y_off || !out_lens))) return LCS_ERR_INVALID;

@@ -22,7 +22,7 @@ TRACEBACK = 1
 # Every function declared in include/lcs.h.
 EXPORTS = (
     "lcs_strerror", "lcs_ctx_create", "lcs_ctx_destroy", "lcs_ctx_sync", "lcs_length", "lcs_length_dev",
-    "lcs_traceback", "lcs_traceback_dev", "lcs_batch", "lcs_batch_dev", "lcs_serve_create", "lcs_serve_submit",
+    "lcs_traceback", "lcs_traceback_dev", "lcs_batch", "lcs_batch_dev", "lcs_batch_dev_hoff", "lcs_serve_create", "lcs_serve_submit",
     "lcs_serve_poll", "lcs_serve_wait", "lcs_result_release", "lcs_serve_destroy", "lcs_ctx_set_profiling",
     "lcs_ctx_last_profile", "lcs_tables", "lcs_tables_dev", "lcs_ctx_get_fill_config", "lcs_ctx_set_fill_config",
     "lcs_ctx_autotune_dev", "lcs_ctx_get_batch_config", "lcs_ctx_set_batch_config", "lcs_ctx_autotune_batch_dev",
@@ -84,6 +84,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lcs_traceback_dev": (ctypes.c_int, [vp, vp, u64, vp, u64, vp, u64, vp, vp]),
         "lcs_batch": (ctypes.c_int, [vp, u8p, u64p, u8p, u64p, u64, u64p]),
         "lcs_batch_dev": (ctypes.c_int, [vp, vp, vp, vp, vp, u64, vp, vp]),
+        "lcs_batch_dev_hoff": (ctypes.c_int, [vp, vp, vp, vp, vp, u64, vp, vp]),
         "lcs_serve_create": (ctypes.c_int, [vp, ctypes.POINTER(ServeCfg), ctypes.POINTER(vp)]),
         "lcs_serve_submit": (ctypes.c_int, [vp, u8p, u64, u8p, u64, u32, u64p]),
         "lcs_serve_poll": (ctypes.c_int, [vp, u64, ctypes.POINTER(Result)]),
@@ -335,6 +336,15 @@ class Context:
                                 ctypes.c_void_p(ys.data_ptr()), ctypes.c_void_p(y_off.data_ptr()), count,
                                 ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream))
         _check(rc, "lcs_batch_dev")
+
+    def batch_dev_hoff(self, xs, x_off, ys, y_off, count: int, out, stream=None) -> None:
+        """xs, ys, out: CUDA tensors; x_off, y_off: host uint64 arrays of count + 1 offsets (lcs_batch_dev_hoff)."""
+        xo = np.ascontiguousarray(x_off, dtype=np.uint64)
+        yo = np.ascontiguousarray(y_off, dtype=np.uint64)
+        rc = _lib.lcs_batch_dev_hoff(self._h, ctypes.c_void_p(xs.data_ptr()), xo.ctypes.data_as(ctypes.c_void_p),
+                                     ctypes.c_void_p(ys.data_ptr()), yo.ctypes.data_as(ctypes.c_void_p), count,
+                                     ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream))
+        _check(rc, "lcs_batch_dev_hoff")
 
 
 class Server:

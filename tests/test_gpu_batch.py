@@ -47,22 +47,45 @@ def test_batch_mixed_alphabets_in_one_launch(ctx, oracle):
     assert [int(v) for v in got] == [oracle.lcs_length(x, y) for x, y in pairs]
 
 
-def test_batch_dev_matches_host(ctx):
+def test_batch_dev_and_host_offsets_vs_oracle(ctx, oracle):
+    """lcs_batch_dev (offsets on the device) and lcs_batch_dev_hoff (offsets in host memory, starting past a few
+    leading bytes of the buffers), each called twice (a planning call, then the cached plan replayed as a graph),
+    every length against the oracle."""
     import torch
     pairs = gen.batch_pairs(count=500, seed=123)
-    host = ctx.batch(pairs)
-    xs = np.concatenate([x for x, _ in pairs])
-    ys = np.concatenate([y for _, y in pairs])
+    want = np.array([oracle.lcs_length(x, y) for x, y in pairs], np.int64)
+    lead_x, lead_y = 7, 3  # bytes in front of the first pair
+    xs = np.concatenate([np.full(lead_x, 65, np.uint8)] + [x for x, _ in pairs])
+    ys = np.concatenate([np.full(lead_y, 67, np.uint8)] + [y for _, y in pairs])
     xo = np.zeros(len(pairs) + 1, np.int64)
     yo = np.zeros(len(pairs) + 1, np.int64)
     xo[1:] = np.cumsum([len(x) for x, _ in pairs])
     yo[1:] = np.cumsum([len(y) for _, y in pairs])
+    xo += lead_x
+    yo += lead_y
     d = torch.device("cuda", 0)
+    dxs, dys = torch.from_numpy(xs).to(d), torch.from_numpy(ys).to(d)
     out = torch.zeros(len(pairs), dtype=torch.int64, device=d)
-    ctx.batch_dev(torch.from_numpy(xs).to(d), torch.from_numpy(xo).to(d), torch.from_numpy(ys).to(d),
-                  torch.from_numpy(yo).to(d), len(pairs), out)
-    ctx.sync()
-    assert np.array_equal(out.cpu().numpy(), host.astype(np.int64))
+    for _ in range(2):
+        out.zero_()
+        ctx.batch_dev(dxs, torch.from_numpy(xo).to(d), dys, torch.from_numpy(yo).to(d), len(pairs), out)
+        ctx.sync()
+        assert np.array_equal(out.cpu().numpy(), want)
+    for _ in range(2):
+        out.zero_()
+        ctx.batch_dev_hoff(dxs, xo.astype(np.uint64), dys, yo.astype(np.uint64), len(pairs), out)
+        ctx.sync()
+        assert np.array_equal(out.cpu().numpy(), want)
+
+
+def test_batch_dev_hoff_rejects_bad_offsets(ctx):
+    import torch
+    from paper_1306_4627_gb300 import lcs
+    d = torch.device("cuda", 0)
+    buf = torch.zeros(16, dtype=torch.uint8, device=d)
+    out = torch.zeros(2, dtype=torch.int64, device=d)
+    with pytest.raises(lcs.LCSError):  # decreasing offsets
+        ctx.batch_dev_hoff(buf, np.array([0, 8, 4], np.uint64), buf, np.array([0, 4, 8], np.uint64), 2, out)
 
 
 def test_batch_matches_single_pair_path(ctx):
