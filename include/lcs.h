@@ -170,7 +170,7 @@ LCS_API int lcs_length_dev(lcs_ctx* ctx, const uint8_t* d_x, uint64_t m, const u
  *   - Limit: m, n <= 65536; larger sizes are rejected with LCS_ERR_INVALID.
  *   - Scratch: a 6.5 MiB array that the library reserves statically in device memory. Every GPU that loads the
  *     library holds it until the process exits. The first call on a device, made with that device current, looks up
- *     the array's device address; make that first call before any stream capture.
+ *     the array's device address (a runtime query).
  *   - The array is shared by all calls on a device and keeps the last call's contents (each call clears what must
  *     start at zero). Calls that overlapped on the GPU would race on it; this entry point therefore serialises its
  *     calls per device and waits for each one.
