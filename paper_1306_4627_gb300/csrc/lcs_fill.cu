@@ -703,9 +703,9 @@ int fill_max_coop_blocks(int device) {
   return sms * per_sm;
 }
 
-// B = rows per step (8 or 16); variant bits 1-2 choose the hand-off validation group of ring-fed warps: 0 = the
-// default (16 steps for B = 8, 8 for B = 16), otherwise 1 = the smaller (8 / 8), 2 = the larger (32 / 16). All
-// give the same results; only the pipeline lag and the per-step overhead differ.
+// B = rows per step (8 or 16); variant bits 1-2 choose the hand-off validation group of ring-fed warps: 2 = the
+// larger (32 steps for B = 8, 16 for B = 16), any other value the default (16 / 8). Both give the same results;
+// only the pipeline lag and the per-step overhead differ.
 template <int B, int VGD, int VGA>
 cudaError_t launch_b(const FillArgs& a, bool traceback, cudaStream_t st) {
   const int sel = (a.variant >> 1) & 3;
