@@ -64,11 +64,11 @@ struct BatchArgs {
 constexpr uint32_t kMaxBatchCols = kRowWords * 32;  // 4096: the longest y of a batch pair
 
 
-// One match-mask table (see the comment in k_batch_prep): column j of the table has the code ycode[j], or
-// ycode[n - 1 - j] for the table over reversed y. The words are independent; four are in flight at a time.
+// One match-mask table (see the comment in k_batch_prep): column j of the table has the code map[y[j]], or
+// map[y[n - 1 - j]] for the table over reversed y. The words are independent; four are in flight at a time.
 template <int NB>
-__device__ __forceinline__ void build_table(uint32_t* tab, const BPair& pr, bool reversed, const uint8_t* ycode,
-                                            uint32_t sigma, uint32_t lane) {
+__device__ __forceinline__ void build_table(uint32_t* tab, const BPair& pr, bool reversed, const uint8_t* ysh,
+                                            const uint16_t* map, uint32_t sigma, uint32_t lane) {
   uint32_t flip0[NB];  // for row r = lane: 0 where bit b of r is set, all ones where it is not
 #pragma unroll
   for (int b = 0; b < NB; ++b) flip0[b] = ((lane >> b) & 1u) - 1u;
@@ -77,7 +77,7 @@ __device__ __forceinline__ void build_table(uint32_t* tab, const BPair& pr, bool
     const uint32_t j = q * 32 + lane;
     const bool in = j < pr.n;
     const uint32_t valid = __ballot_sync(kFull, in);
-    const uint32_t code = in ? ycode[reversed ? pr.n - 1 - j : j] : 0u;
+    const uint32_t code = in ? map[ysh[reversed ? pr.n - 1 - j : j]] : 0u;
     uint32_t pf[NB];
 #pragma unroll
     for (int b = 0; b < NB; ++b) pf[b] = __ballot_sync(kFull, (code >> b) & 1u);
@@ -97,10 +97,10 @@ __device__ __forceinline__ void build_table(uint32_t* tab, const BPair& pr, bool
 }
 
 template <int NB>
-__device__ __noinline__ void build_tables(const BatchArgs& a, const BPair& pr, const uint8_t* ycode, uint32_t sigma,
-                                          uint32_t lane) {
-  build_table<NB>(a.peq + pr.peq_off, pr, false, ycode, sigma, lane);
-  if (pr.mt < pr.m) build_table<NB>(a.peq + pr.peqr_off, pr, true, ycode, sigma, lane);
+__device__ __noinline__ void build_tables(const BatchArgs& a, const BPair& pr, const uint8_t* ysh, const uint16_t* map,
+                                          uint32_t sigma, uint32_t lane) {
+  build_table<NB>(a.peq + pr.peq_off, pr, false, ysh, map, sigma, lane);
+  if (pr.mt < pr.m) build_table<NB>(a.peq + pr.peqr_off, pr, true, ysh, map, sigma, lane);
 }
 
 __global__ void __launch_bounds__(256, 4) k_batch_prep(BatchArgs a) {
@@ -133,15 +133,23 @@ __global__ void __launch_bounds__(256, 4) k_batch_prep(BatchArgs a) {
       if (lane < 16 && j < pr.n) ysh[j] = y[j];
     }
     __syncwarp();
-    // presence of each byte value: first which 32-value blocks occur, then one pass per occurring block (few for
-    // text alphabets), or one pass with a register per block when more than two blocks occur
+    // presence of each byte value: which 32-value blocks occur, and the OR of the values' low five bits, which is
+    // the presence mask itself when a single block occurs (uppercase DNA or protein letters); otherwise one pass per
+    // occurring block (few for text alphabets), or one pass with a register per block when more than two occur
     {
       if (lane < 8) pres[lane] = 0;
-      uint32_t blocks = 0;
-      for (uint32_t j = lane; j < pr.n; j += 32) blocks |= 1u << (ysh[j] >> 5);
+      uint32_t blocks = 0, low = 0;
+      for (uint32_t j = lane; j < pr.n; j += 32) {
+        const uint32_t v = ysh[j];
+        blocks |= 1u << (v >> 5);
+        low |= 1u << (v & 31);
+      }
       blocks = __reduce_or_sync(kFull, blocks);
+      low = __reduce_or_sync(kFull, low);
       __syncwarp();
-      if (__popc(blocks) <= 2) {
+      if (__popc(blocks) == 1) {
+        if (lane == 0) pres[__ffs(blocks) - 1] = low;
+      } else if (__popc(blocks) == 2) {
         for (uint32_t bl = blocks; bl; bl &= bl - 1) {
           const uint32_t hi = __ffs(bl) - 1;
           uint32_t acc = 0;
@@ -185,9 +193,6 @@ __global__ void __launch_bounds__(256, 4) k_batch_prep(BatchArgs a) {
       }
     }
     if (lane == 0) a.sigma[p] = sigma;
-    __syncwarp();
-    // y's bytes become their codes in place (the codes of y's columns are below sigma <= 256, so they fit a byte)
-    for (uint32_t j = lane; j < pr.n; j += 32) ysh[j] = (uint8_t)map[ysh[j]];
     __syncwarp();
     // codes of the forward job's rows x[0..mt), 16 symbols per load where the alignment of x allows, then of the
     // reverse job's rows x[m-1] down to x[mt]; each list has kCodePadFront zero-row codes before it and
@@ -245,15 +250,15 @@ __global__ void __launch_bounds__(256, 4) k_batch_prep(BatchArgs a) {
     // per pass); row sigma matches no column, since the columns' codes are 0..sigma-1, and comes out zero.
     const uint32_t nb = 32 - __clz(sigma);  // bits of the codes 0..sigma
     switch (nb) {
-      case 1: build_tables<1>(a, pr, ysh, sigma, lane); break;
-      case 2: build_tables<2>(a, pr, ysh, sigma, lane); break;
-      case 3: build_tables<3>(a, pr, ysh, sigma, lane); break;
-      case 4: build_tables<4>(a, pr, ysh, sigma, lane); break;
-      case 5: build_tables<5>(a, pr, ysh, sigma, lane); break;
-      case 6: build_tables<6>(a, pr, ysh, sigma, lane); break;
-      case 7: build_tables<7>(a, pr, ysh, sigma, lane); break;
-      case 8: build_tables<8>(a, pr, ysh, sigma, lane); break;
-      default: build_tables<9>(a, pr, ysh, sigma, lane); break;
+      case 1: build_tables<1>(a, pr, ysh, map, sigma, lane); break;
+      case 2: build_tables<2>(a, pr, ysh, map, sigma, lane); break;
+      case 3: build_tables<3>(a, pr, ysh, map, sigma, lane); break;
+      case 4: build_tables<4>(a, pr, ysh, map, sigma, lane); break;
+      case 5: build_tables<5>(a, pr, ysh, map, sigma, lane); break;
+      case 6: build_tables<6>(a, pr, ysh, map, sigma, lane); break;
+      case 7: build_tables<7>(a, pr, ysh, map, sigma, lane); break;
+      case 8: build_tables<8>(a, pr, ysh, map, sigma, lane); break;
+      default: build_tables<9>(a, pr, ysh, map, sigma, lane); break;
     }
     __syncwarp();
   }

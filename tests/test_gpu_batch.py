@@ -27,14 +27,20 @@ def test_batch_edge_shapes(ctx, oracle):
         assert int(g) == oracle.lcs_length(x, y), (len(x), len(y))
 
 
-@pytest.mark.parametrize("sigma", [2, 4, 20, 256])
+# alphabets by the 32-value blocks of byte values they occupy (the prep's alphabet pass has a path for one block,
+# one for two and one for more): "AB", DNA and protein letters one block each, mixed-case DNA two, digits with
+# mixed-case letters three, all bytes eight
+ALPHABETS = {2: b"AB", 4: gen.DNA, 20: gen.PROTEIN, 256: gen.BYTES, "2blk": b"ACGTacgt", "3blk": b"09AZaz"}
+
+
+@pytest.mark.parametrize("sigma", [2, 4, 20, 256, "2blk", "3blk"])
 def test_batch_random_mixed(ctx, oracle, sigma):
-    rng = np.random.default_rng(sigma)
+    rng = np.random.default_rng(len(ALPHABETS[sigma]))
     pairs = []
     for k in range(300):
         m = int(rng.integers(1, 700))
         n = int(rng.integers(1, 1500))
-        alpha = {2: b"AB", 4: gen.DNA, 20: gen.PROTEIN, 256: gen.BYTES}[sigma]
+        alpha = ALPHABETS[sigma]
         pairs.append((gen.random_string(5000 + 2 * k, m, alpha), gen.random_string(5001 + 2 * k, n, alpha)))
     got = ctx.batch(pairs)
     want = [oracle.lcs_length(x, y) for x, y in pairs]
