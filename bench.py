@@ -769,7 +769,9 @@ def measure_batch(args, dev, probes=None, min_s=1.0, ws=1, rank=0, dist=None) ->
                                 "note": "lcs_length_dev per pair, back to back, same GPU"},
         "e2e": {"value": total_cells / e2e_s / 1e9, "unit": "GCUPS", "stat": "median of the timed calls",
                 "calls": len(e2e), "h2d_bytes_per_step": int(xs.nbytes + ys.nbytes),
-                "d2h_bytes_per_step": 8 * len(pairs)},
+                "d2h_bytes_per_step": 8 * len(pairs),
+                "transfer": "lcs_batch on page-locked host buffers: the kernels read the strings in place over the "
+                            "host link (no copy into device buffers first), the lengths come back by one copy"},
         "cpu_baseline": cpu,
         "gpu_launches": 3 * len(tot), "clocks": clocks,  # k_batch_prep, k_batch_main, k_batch_combine per call
     }

@@ -216,7 +216,10 @@ LCS_API int lcs_tables_dev(lcs_ctx* ctx, const uint8_t* d_x, uint64_t m, const u
 /* ---- batch: many independent pairs, lengths only (c[m_k, n_k] for every pair k) ------------------------------- */
 
 /* Pair k is x = xs[x_off[k] .. x_off[k+1]) and y = ys[y_off[k] .. y_off[k+1]) (count+1 offsets each, non-
- * decreasing, host memory). out_lens[k] receives its LCS length. Blocking. Errors: LCS_ERR_INVALID (bad offsets),
+ * decreasing, host memory). out_lens[k] receives its LCS length. Blocking. When both string ranges are page-locked
+ * host memory mapped for the device (cudaMallocHost / cudaHostAlloc / cudaHostRegister), the kernels read them in
+ * place over the host link and nothing is copied into device buffers first; pageable strings are copied (small
+ * batches through a page-locked staging area of the context). Errors: LCS_ERR_INVALID (bad offsets),
  * LCS_ERR_NOMEM, LCS_ERR_CUDA, LCS_ERR_TIMEOUT. */
 LCS_API int lcs_batch(lcs_ctx* ctx, const uint8_t* xs, const uint64_t* x_off, const uint8_t* ys, const uint64_t* y_off,
               uint64_t count, uint64_t* out_lens);

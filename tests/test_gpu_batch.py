@@ -127,3 +127,29 @@ def test_batch_split_pairs(ctx, oracle, sigma):
     for _ in range(3):  # first call plans and launches; the repeats replay the recorded launches
         got = ctx.batch(pairs)
         assert [int(v) for v in got] == want
+
+
+def test_batch_page_locked_buffers_read_in_place(ctx, oracle):
+    """lcs_batch on page-locked host buffers, which the kernels read in place over the host link instead of a copy
+    into device buffers: bytes in front of the first pair, empty pairs, a pair wider than 4096 columns (it takes the
+    single-pair path, reading in place as well); the first call plans and the repeats replay the recorded launches.
+    Every length equals the oracle's and the same batch's from pageable buffers."""
+    import torch
+    pairs = gen.batch_pairs(count=300, seed=77)
+    pairs += [gen.pair_uniform(900, 5000, 4, seed=78), gen.pair_uniform(0, 40, 4, seed=79),
+              gen.pair_uniform(35, 0, 20, seed=80)]
+    want = np.array([oracle.lcs_length(x, y) for x, y in pairs], np.uint64)
+    lead_x, lead_y = 5, 11
+    xs = np.concatenate([np.full(lead_x, 71, np.uint8)] + [x for x, _ in pairs])
+    ys = np.concatenate([np.full(lead_y, 84, np.uint8)] + [y for _, y in pairs])
+    xo = np.zeros(len(pairs) + 1, np.uint64)
+    yo = np.zeros(len(pairs) + 1, np.uint64)
+    xo[1:] = np.cumsum([len(x) for x, _ in pairs])
+    yo[1:] = np.cumsum([len(y) for _, y in pairs])
+    xo += lead_x
+    yo += lead_y
+    xs_pinned = torch.from_numpy(xs).pin_memory()
+    ys_pinned = torch.from_numpy(ys).pin_memory()
+    for _ in range(3):
+        assert np.array_equal(ctx.batch_concat(xs_pinned.numpy(), xo, ys_pinned.numpy(), yo), want)
+    assert np.array_equal(ctx.batch_concat(xs, xo, ys, yo), want)
