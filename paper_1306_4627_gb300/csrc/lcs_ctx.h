@@ -71,6 +71,11 @@ struct lcs_ctx {
   uint64_t bcells = 0, bblocks = 0, bnpairs = 0, bnitems = 0, bnsplit = 0;
   uint64_t bjobs_at = 0, bitems_at = 0, bsplit_at = 0, border_at = 0;  // byte offsets of the plan's parts in bplan
   cudaStream_t cap_stream = nullptr;
+  // single-pair calls: the last call's arguments (pseen), and the launches of a call that repeated them captured as a
+  // CUDA graph (pexec, for the arguments pkey), replayed while they keep repeating; pgraph_off after a failed capture
+  std::vector<uint64_t> pseen, pkey;
+  cudaGraphExec_t pexec = nullptr;
+  bool pgraph_off = false;
   // pinned host memory: the status word and result length of a call (fetched together), and a staging area for
   // host-buffer calls' inputs and traceback output (copies from pinned memory run asynchronously)
   uint64_t* host_tail = nullptr;  // 8 words
@@ -108,6 +113,10 @@ struct lcs_ctx {
     if (bexec) cudaGraphExecDestroy(bexec);
     bexec = nullptr;
     bvalid = false;
+    if (pexec) cudaGraphExecDestroy(pexec);
+    pexec = nullptr;
+    pkey.clear();
+    pseen.clear();
     if (cap_stream) cudaStreamDestroy(cap_stream);
     cap_stream = nullptr;
     lcs::DBuf* all[] = {&small, &x, &y, &out, &xoff_f, &xoff_r, &xcode, &peq_f, &peq_r, &carry_f, &carry_r,

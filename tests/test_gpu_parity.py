@@ -229,3 +229,51 @@ def test_small_path_alphabets_and_related(ctx, ctx_general, oracle, sigma):
     for c in (ctx, ctx_general):
         check_pair(c, oracle, x, y)
         check_pair(c, oracle, y, x)
+
+
+@pytest.mark.parametrize("m,n,sigma", [(2048, 2048, 4), (3001, 1500, 20), (1200, 5000, 256), (70000, 300, 4)])
+def test_repeated_arguments_replay_a_graph(ctx, oracle, m, n, sigma):
+    """Calls that repeat the previous call's arguments: the second one captures its launches as a CUDA graph and
+    later ones replay it. New strings written into the same device buffers between calls, four traceback calls in a
+    row, then four length calls in a row, then host-buffer calls of one shape; every result equals the oracle's."""
+    import torch
+    d = torch.device("cuda", 0)
+    dx = torch.empty(m, dtype=torch.uint8, device=d)
+    dy = torch.empty(n, dtype=torch.uint8, device=d)
+    out = torch.zeros(min(m, n), dtype=torch.uint8, device=d)
+    out_len = torch.zeros(1, dtype=torch.int64, device=d)
+    pairs = [gen.pair_uniform(m, n, sigma, seed=7700 + 10 * k + sigma) for k in range(4)]
+    for x, y in pairs:
+        dx.copy_(torch.from_numpy(x))
+        dy.copy_(torch.from_numpy(y))
+        ctx.traceback_dev(dx, dy, out, out_len)
+        ctx.sync()
+        L = int(out_len.item())
+        assert bytes(out[:L].cpu().numpy()) == oracle.lcs_traceback(x, y)
+    for x, y in pairs:
+        dx.copy_(torch.from_numpy(x))
+        dy.copy_(torch.from_numpy(y))
+        ctx.length_dev(dx, dy, out_len)
+        ctx.sync()
+        assert int(out_len.item()) == oracle.lcs_length(x, y)
+    for x, y in pairs[:3]:
+        assert ctx.traceback(x, y) == oracle.lcs_traceback(x, y)
+
+
+def test_direct_launches_match_replayed_graph(oracle):
+    """The same repeated calls on a context that never captures (LCS_NO_PAIR_GRAPH=1) give the same results."""
+    from paper_1306_4627_gb300 import lcs
+    os.environ["LCS_NO_PAIR_GRAPH"] = "1"
+    try:
+        direct = lcs.Context(0)
+    finally:
+        del os.environ["LCS_NO_PAIR_GRAPH"]
+    pairs = [gen.pair_uniform(4000, 3000, 4, seed=7800 + k) for k in range(3)]
+    with lcs.Context(0) as graphed:
+        for x, y in pairs:
+            want = oracle.lcs_traceback(x, y)
+            assert direct.traceback(x, y) == want
+            assert graphed.traceback(x, y) == want
+        for x, y in pairs:
+            assert direct.length(y, x) == graphed.length(y, x) == oracle.lcs_length(x, y)
+    direct.close()
