@@ -126,6 +126,10 @@ int run_fill(lcs_ctx* c, FillJob* jobs, int njobs, bool traceback, uint32_t B, c
   a.spin_limit = c->spin_limit;
   a.variant = traceback ? c->fill_variant_tb : c->fill_variant;
   a.debug_drop = c->debug_drop;
+  // traceback segments of fewer than 32 row-blocks need the dense snapshots (every 8 row-blocks); a period past the
+  // last row (the table export: no snapshot at all) does not
+  a.dense_snap =
+      (traceback && jobs[0].snap && jobs[0].snap_rb % 32 != 0 && jobs[0].snap_rb <= jobs[0].R) ? 1u : 0u;
   uint32_t total = 0;
   for (int k = 0; k < njobs; ++k) total += jobs[k].nblocks_total;
   if (total <= (uint32_t)c->max_coop) {
@@ -285,7 +289,8 @@ int run_length(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, u
 }
 
 // Geometry of a traceback call. Segments of H rows for the parallel walk, at most kMaxSegments of them. H is a
-// multiple of 32 * B: the fill kernel snapshots a lane's word once per 32 steps.
+// multiple of 32 * B (the fill snapshots a lane's word once per 32 steps) or, when that allows more and shorter
+// segments, of 8 * B (the fill's dense snapshots, every 8 steps).
 struct TbGeo {
   uint32_t B;
   Geo g;
@@ -299,6 +304,12 @@ static TbGeo tb_geo(const lcs_ctx* c, uint64_t m, uint64_t n) {
   T.g = geo_for(n);
   const uint64_t unit = 32ull * T.B;
   T.H = unit * ((m + kMaxSegments * unit - 1) / (kMaxSegments * unit));
+  // Small pairs take shorter segments, down to 8 row-blocks: a walk is a chain of dependent steps, one or more per
+  // row, so its time grows with H, and for a short fill the walks are a large share of the call. The fill then
+  // snapshots every 8 row-blocks, which costs it 7-12 % more per step (measured), so larger pairs keep 32.
+  const uint64_t unit8 = 8ull * T.B;
+  const uint64_t Hd = unit8 * ((m + kMaxSegments * unit8 - 1) / (kMaxSegments * unit8));
+  if (c->dense_snap && m <= kDenseSnapMaxRows && m * n <= kDenseSnapMaxCells && Hd < T.H) T.H = Hd;
   T.S = (m + T.H - 1) / T.H;
   T.rev = T.S > 1;
   T.Rf = (m + T.B - 1) / T.B;
@@ -307,7 +318,8 @@ static TbGeo tb_geo(const lcs_ctx* c, uint64_t m, uint64_t n) {
   const uint64_t nwarps = T.g.nblocks * kFillWarps;
   T.t_bytes = (size_t)nwarps * (T.Rf + 31) * 32 * T.B * 4;
   // walkers per segment: as many as the corridor can have columns (n + 1), within the budget
-  uint64_t W = std::min<uint64_t>(n + 1, std::min<uint64_t>(kMaxWalkersPerSeg, kWalkerBudget / T.S));
+  const uint64_t budget = T.H % unit ? kWalkerBudgetDense : kWalkerBudget;  // more segments, as many walkers each
+  uint64_t W = std::min<uint64_t>(n + 1, std::min<uint64_t>(kMaxWalkersPerSeg, budget / T.S));
   T.W = std::max<uint64_t>(kWalkers, (W + kWalkers - 1) / kWalkers * kWalkers);
   return T;
 }
@@ -348,6 +360,7 @@ uint64_t traceback_bitmap_bytes(const lcs_ctx* c, uint64_t m, uint64_t n) {
 // direction bitmap, so that such calls allocate nothing (the growth keeps a margin for the few shapes whose
 // walker buffers exceed those of (max_m, max_n) slightly).
 int presize(lcs_ctx* c, uint64_t max_m, uint64_t max_n) {
+  c->dense_snap = false;  // the segment geometry of (max_m, max_n) then bounds every smaller call's walker buffers
   int rc = ensure_len(c, len_geo(c, max_m, max_n));
   if (!rc) rc = ensure_tb(c, tb_geo(c, max_m, max_n), max_m, false);
   if (!rc) rc = from_cuda(ensure(c->x, std::max<uint64_t>(max_m, 1)));
@@ -594,6 +607,8 @@ extern "C" int lcs_ctx_create(int device, lcs_ctx** out) {
   if (const char* e = getenv("LCS_NO_SMALL_PATH")) c->small_path = atoi(e) == 0;
   // every single-pair call launched directly, never replayed as a graph (for comparisons)
   if (const char* e = getenv("LCS_NO_PAIR_GRAPH")) c->pgraph_off = atoi(e) != 0;
+  // traceback segments of at least 32 row-blocks whatever the size (for comparisons)
+  if (const char* e = getenv("LCS_NO_DENSE_SNAP")) c->dense_snap = atoi(e) == 0;
   *out = c;
   return LCS_OK;
 }

@@ -53,6 +53,7 @@ struct lcs_ctx {
   uint32_t bk_max = 4;  // the planned batch's largest words per lane
   uint32_t debug_drop = 0;    // test hook (environment LCS_DEBUG_DROP_HANDOFF): a hand-off that never comes
   bool small_path = true;     // small pairs in one launch (lcs_small.cu); environment LCS_NO_SMALL_PATH=1 turns it off
+  bool dense_snap = true;     // traceback segments of 8 row-blocks and up (else 32 and up); LCS_NO_DENSE_SNAP=1: off
   // host-buffer calls wait for their stream by a spin (lowest latency) or, when set (the server's workers: many
   // contexts waiting at once on few host cores), by sleeping on an event recorded with blocking synchronisation
   bool blocking_wait = false;

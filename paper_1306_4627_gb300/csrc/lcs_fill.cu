@@ -42,6 +42,11 @@ __device__ __forceinline__ void st_relaxed_gpu_if(uint32_t* p, uint32_t v, uint3
       "r"(pred)
       : "memory");
 }
+// Predicated plain store (no branch around it): stores only when pred != 0.
+__device__ __forceinline__ void st_global_if(uint32_t* p, uint32_t v, uint32_t pred) {
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.global.u32 [%0], %1;\n\t}" ::"l"(p), "r"(v), "r"(pred)
+               : "memory");
+}
 __device__ __forceinline__ uint32_t lds_vol_u32(uint32_t saddr) {
   uint32_t v;
   asm volatile("ld.volatile.shared.u32 %0, [%1];" : "=r"(v) : "r"(saddr) : "memory");
@@ -129,6 +134,8 @@ struct Lane {
                       // window one step ahead, or right after a validation at a window or group start
   uint32_t cap;       // V captured at the end of this lane's row-block r with (r + 1) % 32 == 0 in this block
   uint32_t xstage[16];  // symbol offsets of row-block t0 + 34 + lane, staged for the next 32-step boundary
+  int32_t nsnap;      // dense snapshots: the next row-block whose end row is snapshotted, and where its word goes
+  uint32_t* snp;
   uint4* tp;          // this step's bitmap chunk of the warp, plus this lane's offset
   bool failed;
 };
@@ -194,7 +201,7 @@ __device__ __forceinline__ void p_from_offsets(const Warp& w, const uint32_t (&x
 // already holds) and the offsets of the step after that, so no step waits on a load. Lane 0 takes the previous
 // warp's carries from the block's window (validated once per block), lane 31 hands its own on; the step has no
 // branches.
-template <int B, bool TB, bool SNAP, int SRC, int DST>
+template <int B, bool TB, bool SNAP, bool DS, int SRC, int DST>
 __device__ __forceinline__ void fill_step(const Warp& w, Lane& s, int32_t t, const uint32_t (&pu)[B],
                                           const uint32_t (&xa)[B], uint32_t (&pl)[B], uint32_t (&xl)[B]) {
   constexpr uint32_t kTagMask = (1u << (32 - B)) - 1u;
@@ -221,7 +228,13 @@ __device__ __forceinline__ void fill_step(const Warp& w, Lane& s, int32_t t, con
     for (int v = 0; v < B / 4; ++v) s.tp[v * 32] = make_uint4(tw[4 * v], tw[4 * v + 1], tw[4 * v + 2], tw[4 * v + 3]);
     s.tp += 8 * B;  // 32 lanes x B words = 8 * B uint4 per step
   }
-  if (SNAP) s.cap = (((uint32_t)t & 31u) == w.cap_k) ? V : s.cap;
+  if (SNAP && !DS) s.cap = (((uint32_t)t & 31u) == w.cap_k) ? V : s.cap;
+  if (SNAP && DS) {  // dense: every snapshotted row-block's word stored as it ends (predicated, no branch)
+    const uint32_t hit = (r == s.nsnap) & (r < w.R);
+    st_global_if(s.snp, V, hit);
+    s.snp += hit ? w.wpad : 0u;
+    s.nsnap += hit ? (int32_t)w.snap_rb : 0;
+  }
   if (DST != kDstNone) {  // lane 31 hands its carries for row-block t - 31 to the next warp
     const uint32_t r31 = (uint32_t)(t - 31);
     const uint32_t v = s.cout | ((r31 + 1u) | 1u) & kTagMask;
@@ -371,7 +384,7 @@ __device__ __forceinline__ void block_start(const Warp& w, Lane& s, int32_t t) {
   }
 }
 
-template <int B, bool TB, int VG, bool SNAP, int SRC, int DST>
+template <int B, bool TB, int VG, bool SNAP, bool DS, int SRC, int DST>
 __device__ __forceinline__ void warp_loop(const Warp& w, Lane& s) {
   static_assert(VG % 4 == 0 && 32 % VG == 0, "validation group: a multiple of 4 steps that divides 32");
   const int32_t lane = (int32_t)w.lane;
@@ -399,14 +412,14 @@ __device__ __forceinline__ void warp_loop(const Warp& w, Lane& s) {
       // eight or sixteen per iteration were slower (1.86 / 2.47 ms against 1.30 ms for the traceback fill)
 #pragma unroll 1
       for (int k = VG * g; k < VG * g + VG; k += 4) {
-        fill_step<B, TB, SNAP, SRC, DST>(w, s, t + k, p0, x1, p1, x0);
-        fill_step<B, TB, SNAP, SRC, DST>(w, s, t + k + 1, p1, x0, p0, x1);
-        fill_step<B, TB, SNAP, SRC, DST>(w, s, t + k + 2, p0, x1, p1, x0);
-        fill_step<B, TB, SNAP, SRC, DST>(w, s, t + k + 3, p1, x0, p0, x1);
+        fill_step<B, TB, SNAP, DS, SRC, DST>(w, s, t + k, p0, x1, p1, x0);
+        fill_step<B, TB, SNAP, DS, SRC, DST>(w, s, t + k + 1, p1, x0, p0, x1);
+        fill_step<B, TB, SNAP, DS, SRC, DST>(w, s, t + k + 2, p0, x1, p1, x0);
+        fill_step<B, TB, SNAP, DS, SRC, DST>(w, s, t + k + 3, p1, x0, p0, x1);
       }
       if (SRC == kSrcGlobal && VG * g + VG == 16) s.win_next = window_load<SRC>(w, t + 32 + lane);  // next window
     }
-    if (SNAP) snap_store(w, s, t, steps);
+    if (SNAP && !DS) snap_store(w, s, t, steps);
   }
   xo_refill<B>(w, s, t);
   window_validate<B, SRC>(w, s, t, t == 0);
@@ -414,26 +427,27 @@ __device__ __forceinline__ void warp_loop(const Warp& w, Lane& s) {
   const int32_t t_tail = t;
   for (; t + 1 < steps; t += 2) {
     if ((t & (VG - 1)) == 0) ring_group_validate<B, SRC, VG>(w, s, t);
-    fill_step<B, TB, SNAP, SRC, DST>(w, s, t, p0, x1, p1, x0);
-    fill_step<B, TB, SNAP, SRC, DST>(w, s, t + 1, p1, x0, p0, x1);
+    fill_step<B, TB, SNAP, DS, SRC, DST>(w, s, t, p0, x1, p1, x0);
+    fill_step<B, TB, SNAP, DS, SRC, DST>(w, s, t + 1, p1, x0, p0, x1);
   }
   if (t < steps) {
     if ((t & (VG - 1)) == 0) ring_group_validate<B, SRC, VG>(w, s, t);
-    fill_step<B, TB, SNAP, SRC, DST>(w, s, t, p0, x1, p1, x0);
+    fill_step<B, TB, SNAP, DS, SRC, DST>(w, s, t, p0, x1, p1, x0);
   }
-  if (SNAP) snap_store(w, s, t_tail, steps);
+  if (SNAP && !DS) snap_store(w, s, t_tail, steps);
 }
 
-template <int B, bool TB, int VG, bool SNAP>
+template <int B, bool TB, int VG, bool SNAP, bool DS>
 __device__ __forceinline__ void dispatch(const Warp& w, Lane& s, bool first_warp, bool last_warp, uint32_t wib) {
-  if (first_warp) warp_loop<B, TB, VG, SNAP, kSrcNone, kDstRing>(w, s);
-  else if (wib == 0) warp_loop<B, TB, VG, SNAP, kSrcGlobal, kDstRing>(w, s);
-  else if (wib + 1 < kFillWarps) warp_loop<B, TB, VG, SNAP, kSrcRing, kDstRing>(w, s);
-  else if (!last_warp) warp_loop<B, TB, VG, SNAP, kSrcRing, kDstGlobal>(w, s);
-  else warp_loop<B, TB, VG, SNAP, kSrcRing, kDstNone>(w, s);
+  if (first_warp) warp_loop<B, TB, VG, SNAP, DS, kSrcNone, kDstRing>(w, s);
+  else if (wib == 0) warp_loop<B, TB, VG, SNAP, DS, kSrcGlobal, kDstRing>(w, s);
+  else if (wib + 1 < kFillWarps) warp_loop<B, TB, VG, SNAP, DS, kSrcRing, kDstRing>(w, s);
+  else if (!last_warp) warp_loop<B, TB, VG, SNAP, DS, kSrcRing, kDstGlobal>(w, s);
+  else warp_loop<B, TB, VG, SNAP, DS, kSrcRing, kDstNone>(w, s);
 }
 
-template <int B, bool TB, int VG>
+// DS: dense snapshots (a traceback's segments shorter than 32 row-blocks), stored as each row-block ends.
+template <int B, bool TB, int VG, bool DS>
 __global__ void __launch_bounds__(kFillThreads, 1) k_fill(const __grid_constant__ FillArgs a) {
   static_assert(B % 4 == 0 && B >= 4 && B <= 16, "row-block height");
   extern __shared__ __align__(16) uint32_t sm[];
@@ -496,13 +510,15 @@ __global__ void __launch_bounds__(kFillThreads, 1) k_fill(const __grid_constant_
   s.win_next = 0;
   s.cin0 = 0;
   s.tp = J.T ? reinterpret_cast<uint4*>(J.T + (gw * (J.R + 31)) * 32 * (uint64_t)B) + lane : nullptr;
+  s.nsnap = (int32_t)J.snap_rb - 1;
+  s.snp = w.snap;
 
   if (TB && J.T) {
-    dispatch<B, true, VG, true>(w, s, first_warp, last_warp, wib);
+    dispatch<B, true, VG, true, DS>(w, s, first_warp, last_warp, wib);
   } else if (TB && J.snap) {  // the table of the reversed strings in a traceback launch: snapshots, no bitmap
-    dispatch<B, false, VG, true>(w, s, first_warp, last_warp, wib);
-  } else {
-    dispatch<B, false, VG, false>(w, s, first_warp, last_warp, wib);
+    dispatch<B, false, VG, true, DS>(w, s, first_warp, last_warp, wib);
+  } else if (!DS) {
+    dispatch<B, false, VG, false, false>(w, s, first_warp, last_warp, wib);
   }
 
   if (J.final_v) J.final_v[gw * 32 + lane] = s.V;
@@ -512,10 +528,13 @@ __global__ void __launch_bounds__(kFillThreads, 1) k_fill(const __grid_constant_
   }
 }
 
-template <int B, bool TB, int VG>
+template <int B, bool TB, int VG, bool DS = false>
 cudaError_t launch_t(const FillArgs& a, cudaStream_t st) {
+  if constexpr (TB && !DS) {
+    if (a.dense_snap) return launch_t<B, true, VG, true>(a, st);
+  }
   static std::atomic<uint64_t> attr_done{0};  // per template instance: devices whose attribute is set
-  auto fn = k_fill<B, TB, VG>;
+  auto fn = k_fill<B, TB, VG, DS>;
   const size_t smem = fill_smem_bytes();
   cudaError_t e = once_per_device_attr(
       [&] { return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); }, attr_done);
@@ -696,7 +715,7 @@ size_t fill_smem_bytes() {
 int fill_max_coop_blocks(int device) {
   int sms = 0, per_sm = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
-  auto fn = k_fill<8, true, 16>;
+  auto fn = k_fill<8, true, 16, false>;
   const size_t smem = fill_smem_bytes();
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kFillThreads, smem) != cudaSuccess) return 0;

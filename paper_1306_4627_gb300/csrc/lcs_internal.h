@@ -58,12 +58,16 @@ struct FillArgs {
   uint32_t spin_limit;      // iterations of a bounded wait before it gives up
   uint32_t variant;         // bit 0: shorter dependent chain per row (same results)
   uint32_t debug_drop;      // test hook: the first warp never hands its carries on (its consumer's wait runs out)
+  uint32_t dense_snap;      // traceback: snapshot rows every 8 row-blocks (snap_rb a multiple of 8) instead of 32
 };
 
 // ---- traceback segment walkers ---------------------------------------------------------------------------------
 constexpr int kWalkers = 32;            // walkers per warp; a segment has W of them (a multiple of 32)
-constexpr int kMaxWalkersPerSeg = 1024; // W <= this, and S * W <= kWalkerBudget
-constexpr int kWalkerBudget = 65536;
+constexpr int kMaxWalkersPerSeg = 1024; // W <= this, and S * W <= kWalkerBudget (kWalkerBudgetDense for segments
+constexpr int kWalkerBudget = 65536;    // of fewer than 32 row-blocks, whose snapshots come every 8 row-blocks)
+constexpr int kWalkerBudgetDense = 1 << 18;
+constexpr uint64_t kDenseSnapMaxRows = 8192;        // traceback pairs with shorter segments: at most this many rows
+constexpr uint64_t kDenseSnapMaxCells = 1ull << 24;  // and cells
 constexpr int kMaxSegments = 256;
 
 struct TraceArgs {

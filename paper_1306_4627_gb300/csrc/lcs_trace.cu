@@ -225,7 +225,7 @@ __device__ __forceinline__ uint32_t p_word(const TraceArgs& a, uint32_t code, in
 
 // Walks rows hi..lo+1 from column e; returns the exit column (at row lo); writes emitted symbols to out_chars.
 // Requires hi a multiple of B and hi - lo a multiple of kWalkGroup (every segment but the last: H is a multiple of
-// 32 B). The rows are taken in aligned groups of kWalkGroup: the bitmap words of a group's rows at one 32-column
+// 8 B). The rows are taken in aligned groups of kWalkGroup: the bitmap words of a group's rows at one 32-column
 // word lie at fixed offsets from one address (the fill's layout below), so the group's bitmap and match-mask words
 // at the walk's current word are requested together, with one address computation; the symbol codes and symbols of
 // the next group (code in bits 0-7, symbol in bits 8-15) are requested a group ahead. When the walk moves to

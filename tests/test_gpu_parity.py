@@ -277,3 +277,22 @@ def test_direct_launches_match_replayed_graph(oracle):
         for x, y in pairs:
             assert direct.length(y, x) == graphed.length(y, x) == oracle.lcs_length(x, y)
     direct.close()
+
+
+def test_segment_geometries_agree(oracle):
+    """Small traceback pairs walk segments of 8 row-blocks and up (the fill snapshots every 8 row-blocks); a context
+    with LCS_NO_DENSE_SNAP=1 keeps segments of 32 row-blocks and up. Both give the oracle's string."""
+    from paper_1306_4627_gb300 import lcs
+    os.environ["LCS_NO_DENSE_SNAP"] = "1"
+    try:
+        sparse = lcs.Context(0)
+    finally:
+        del os.environ["LCS_NO_DENSE_SNAP"]
+    with lcs.Context(0) as dense:
+        for k, (m, n, sigma) in enumerate([(2048, 2048, 4), (1000, 1500, 20), (5000, 400, 4), (8192, 2048, 4),
+                                           (3001, 3001, 256), (700, 4000, 4)]):
+            x, y = gen.pair_uniform(m, n, sigma, seed=7900 + k)
+            want = oracle.lcs_traceback(x, y)
+            assert dense.traceback(x, y) == want, (m, n)
+            assert sparse.traceback(x, y) == want, (m, n)
+    sparse.close()
