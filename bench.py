@@ -56,11 +56,11 @@ WORKLOAD_MUTATED = ("single pair, DNA (sigma=4), m=n=65536, Y = X with 10% subst
                     "LCS length + traceback string")
 METRIC = "LCS GCUPS on 1 GB300 vs int-ALU roofline; serve p50/p99 latency vs per-pair"
 HBM_FALLBACK_GBS = 6800.0
-# library kernel launches per call: k_alphabet, k_peq, k_xoff, k_fill, k_corr_pre, k_corr_cols, k_walk, k_chain,
-# k_finalize (traceback); k_alphabet, k_peq, k_xoff, k_fill and the combine (length, meet in the middle)
-LAUNCHES_TRACEBACK = 9
-LAUNCHES_LENGTH_SPLIT_WIDE = 7  # beyond 2048 words the combine takes three launches
-LAUNCHES_LENGTH_SPLIT = 5
+# library kernel launches per call: k_alphabet, k_xoff (masks and row offsets), k_fill, k_corr_pre, k_corr_cols,
+# k_walk, k_chain, k_finalize (traceback); k_alphabet, k_xoff, k_fill and the combine (length, meet in the middle)
+LAUNCHES_TRACEBACK = 8
+LAUNCHES_LENGTH_SPLIT_WIDE = 6  # beyond 2048 words the combine takes three launches
+LAUNCHES_LENGTH_SPLIT = 4
 
 
 def pair_inputs(args, gen):

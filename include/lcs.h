@@ -156,7 +156,7 @@ LCS_API int lcs_probe_step_masks(int device, uint32_t source, uint32_t steps, do
 /* Repeated calls (lcs_length*, lcs_traceback*): a call that repeats the previous call on the context with the same
  * arguments (the same buffers, sizes and outputs; host-buffer calls of one shape stage into the context's own
  * buffers, so they repeat too) is captured once as a CUDA graph, on its second occurrence, and replayed with one
- * launch from then on, instead of nine launches. The graph reads the buffers' contents when it runs. The capture
+ * launch from then on, instead of eight launches. The graph reads the buffers' contents when it runs. The capture
  * costs one extra host step once per new set of arguments; LCS_NO_PAIR_GRAPH=1 in the environment at context
  * creation turns it off. Pairs of the one-launch small path (see lcs_traceback) are never captured. */
 

@@ -166,16 +166,15 @@ static Geo geo_for(uint64_t n) {
   return g;
 }
 
-// Prepares the alphabet, the match masks of Y (forward and, if wanted, reversed) into the context buffers.
-static int prep_y(lcs_ctx* c, const uint8_t* d_y, uint64_t n, const Geo& g, bool want_rev, cudaStream_t st) {
+// Prepares the alphabet of Y and the context's mask buffers; the masks of Y (forward and, if wanted, reversed) are
+// built by the row-offset launch, as the returned job describes.
+static int prep_y(lcs_ctx* c, const uint8_t* d_y, uint64_t n, const Geo& g, bool want_rev, PeqJob* pj,
+                  cudaStream_t st) {
   int rc = from_cuda(ensure(c->peq_f, (size_t)kSigmaMax * g.wpad * 4));
   if (!rc && want_rev) rc = from_cuda(ensure(c->peq_r, (size_t)kSigmaMax * g.wpad * 4));
   if (rc) return rc;
-  rc = from_cuda(launch_alphabet(d_y, n, c->presence(), c->codemap(), c->sigma(), st));
-  if (!rc)
-    rc = from_cuda(launch_peq(d_y, n, g.wpad, c->codemap(), c->sigma(), (uint32_t*)c->peq_f.p,
-                              want_rev ? (uint32_t*)c->peq_r.p : nullptr, st));
-  return rc;
+  *pj = PeqJob{d_y, n, g.wpad, (uint32_t*)c->peq_f.p, want_rev ? (uint32_t*)c->peq_r.p : nullptr};
+  return from_cuda(launch_alphabet(d_y, n, c->presence(), c->codemap(), c->sigma(), st));
 }
 
 // A small pair in one launch (lcs_small.cu): its stages are all under the fill's marks.
@@ -242,14 +241,15 @@ int run_length(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, u
   const uint64_t mt = LG.mt, mb = LG.mb, Rf = LG.Rf, padr = LG.padr, Rr = LG.Rr;
   c->mark(0, st);
   int rc = ensure_len(c, LG);
-  if (!rc) rc = prep_y(c, d_y, n, g, split, st);
+  PeqJob pj{};
+  if (!rc) rc = prep_y(c, d_y, n, g, split, &pj, st);
   if (rc) return rc;
   {  // row offsets of both tables; the hand-off slots and the length accumulator start at zero
     const XoffJob xj[2] = {{d_x, mt, 0, 0, Rf, (uint32_t*)c->xoff_f.p, nullptr},
                            {d_x + mt, mb, 1, padr, Rr, (uint32_t*)c->xoff_r.p, nullptr}};
     const ZeroSpan zs[3] = {{c->carry_f.p, g.nblocks * Rf * 4}, {c->len_acc(), sizeof(unsigned long long)},
                             {c->carry_r.p, g.nblocks * Rr * 4}};
-    rc = from_cuda(launch_xoff(xj, split ? 2 : 1, B, c->codemap(), c->sigma(), zs, split ? 3 : 2, st));
+    rc = from_cuda(launch_xoff(xj, split ? 2 : 1, B, c->codemap(), c->sigma(), zs, split ? 3 : 2, &pj, st));
   }
   if (rc) return rc;
   FillJob jobs[2]{};
@@ -381,14 +381,15 @@ int run_traceback(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y
   const bool rev = TG.rev;
   c->mark(0, st);
   int rc = ensure_tb(c, TG, m, true);
-  if (!rc) rc = prep_y(c, d_y, n, g, rev, st);
+  PeqJob pj{};
+  if (!rc) rc = prep_y(c, d_y, n, g, rev, &pj, st);
   if (rc) return rc;
   {  // row offsets of both tables; hand-off slots, length accumulator and corridor counts start at zero
     const XoffJob xj[2] = {{d_x, m, 0, 0, Rf, (uint32_t*)c->xoff_f.p, (uint8_t*)c->xcode.p},
                            {d_x, m, 1, padr, Rr, (uint32_t*)c->xoff_r.p, nullptr}};
     const ZeroSpan zs[4] = {{c->carry_f.p, g.nblocks * Rf * 4}, {c->len_acc(), sizeof(unsigned long long)},
                             {c->entcnt.p, S * 4}, {c->carry_r.p, g.nblocks * Rr * 4}};
-    rc = from_cuda(launch_xoff(xj, rev ? 2 : 1, B, c->codemap(), c->sigma(), zs, rev ? 4 : 3, st));
+    rc = from_cuda(launch_xoff(xj, rev ? 2 : 1, B, c->codemap(), c->sigma(), zs, rev ? 4 : 3, &pj, st));
   }
   if (rc) return rc;
   FillJob jobs[2]{};
@@ -457,7 +458,7 @@ int run_traceback(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y
 }
 
 // ---- repeated single-pair calls, replayed as a CUDA graph ----------------------------------------------------------
-// A single-pair call on the general path enqueues nine launches, one of them cooperative; for short pairs the host's
+// A single-pair call on the general path enqueues eight launches, one of them cooperative; for short pairs the host's
 // cost per launch, not the GPU, sets the pace. When a call repeats the previous call's arguments exactly (a caller
 // that reuses its buffers, such as a loop over pairs of one shape, or every host-buffer call of one shape, which
 // stages into the context's own buffers), its launches are captured once as a CUDA graph, and this call and every
@@ -532,7 +533,8 @@ int run_tables(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, u
   const uint64_t Rf = (m + B - 1) / B;
   const uint64_t nwarps = g.nblocks * kFillWarps;
   const size_t t_bytes = (size_t)nwarps * (Rf + 31) * 32 * B * 4;
-  int rc = prep_y(c, d_y, n, g, false, st);
+  PeqJob pj{};
+  int rc = prep_y(c, d_y, n, g, false, &pj, st);
   if (!rc) rc = from_cuda(ensure(c->T, t_bytes));
   if (!rc) rc = from_cuda(ensure(c->xoff_f, (Rf + kPadRowblocks + kPadBackRowblocks) * B * 4));
   if (!rc) rc = from_cuda(ensure(c->carry_f, g.nblocks * Rf * 4));
@@ -542,7 +544,7 @@ int run_tables(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y, u
   {
     const XoffJob xj = {d_x, m, 0, 0, Rf, (uint32_t*)c->xoff_f.p, nullptr};
     const ZeroSpan zs[2] = {{c->carry_f.p, g.nblocks * Rf * 4}, {c->len_acc(), sizeof(unsigned long long)}};
-    rc = from_cuda(launch_xoff(&xj, 1, B, c->codemap(), c->sigma(), zs, 2, st));
+    rc = from_cuda(launch_xoff(&xj, 1, B, c->codemap(), c->sigma(), zs, 2, &pj, st));
   }
   if (rc) return rc;
   FillJob job{};

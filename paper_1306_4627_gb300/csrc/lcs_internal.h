@@ -133,12 +133,19 @@ struct ZeroSpan {  // device words to clear (bytes a multiple of 4)
 
 cudaError_t launch_alphabet(const uint8_t* y, uint64_t n, uint32_t* presence8, uint16_t* codemap,
                             uint32_t* sigma_rows, cudaStream_t st);
-// the row offsets of up to two jobs and the clearing of up to kMaxZeroSpans spans, in one launch
+// The match masks of every symbol row 0..sigma for every word < wpad, over Y into peq_f and, if peq_r is not null,
+// over reversed Y into peq_r.
+struct PeqJob {
+  const uint8_t* y;
+  uint64_t n, wpad;
+  uint32_t* peq_f;
+  uint32_t* peq_r;
+};
+// The match masks (when peq is not null), the row offsets of up to two jobs and the clearing of up to kMaxZeroSpans
+// spans, in one launch (all of it needs only the alphabet).
 cudaError_t launch_xoff(const XoffJob* jobs, int njobs, uint32_t B, const uint16_t* codemap,
-                        const uint32_t* sigma_rows, const ZeroSpan* zero, int nzero, cudaStream_t st);
-// masks of every symbol row 0..sigma for every word < wpad, over Y into peq_f and, if peq_r, over reversed Y
-cudaError_t launch_peq(const uint8_t* y, uint64_t n, uint64_t wpad, const uint16_t* codemap,
-                       const uint32_t* sigma_rows, uint32_t* peq_f, uint32_t* peq_r, cudaStream_t st);
+                        const uint32_t* sigma_rows, const ZeroSpan* zero, int nzero, const PeqJob* peq,
+                        cudaStream_t st);
 // fill
 int fill_max_coop_blocks(int device);
 cudaError_t launch_fill(const FillArgs& a, uint32_t B, bool traceback, cudaStream_t st);

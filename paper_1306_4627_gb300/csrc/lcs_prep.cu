@@ -2,9 +2,11 @@
 // masks Peq (bit k of word q of row s is set when y_{32q+k+1} is symbol s). The match masks realise the test
 // x_i = y_j of LCS-length (paper §I.C, its line "if x_i = y_j") for 32 columns at a time.
 //
-// A call is a handful of launches (the host side of a call, not the GPU, bounds small pairs and busy servers):
-// the alphabet in one block, the masks of both directions in one launch that writes every word (nothing to clear
-// first), and the row offsets of both directions in one launch that also clears the call's scratch words.
+// A call is two launches (the host side of a call, not the GPU, bounds small pairs and busy servers): the alphabet
+// in one block, then one launch that writes the masks of both directions (every word: nothing to clear first) and
+// the row offsets of both directions, and clears the call's scratch words.
+#include <algorithm>
+
 #include "lcs_internal.h"
 
 namespace lcs {
@@ -124,17 +126,27 @@ __global__ void k_codemap(const uint32_t* __restrict__ presence8, uint16_t* __re
 struct XoffArgs {
   XoffJob job[2];
   ZeroSpan zero[kMaxZeroSpans];
-  uint32_t njobs, nzero, B;
+  PeqJob peq;
+  uint32_t njobs, nzero, npeq, B;
   const uint16_t* codemap;
   const uint32_t* sigma_rows;
 };
 
-// blockIdx.y < njobs: the row offsets of that job; the last y slice clears the spans.
+__device__ void peq_slice(const PeqJob& P, bool rev, const uint16_t* __restrict__ codemap,
+                          const uint32_t* __restrict__ sigma_rows);
+
+// blockIdx.y < npeq: the match masks over Y (0) or reversed Y (1); then the row offsets of each job; the last y slice
+// clears the spans.
 __global__ void k_xoff(const __grid_constant__ XoffArgs a) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (blockIdx.y < a.njobs) {
-    const XoffJob& J = a.job[blockIdx.y];
+  if (blockIdx.y < a.npeq) {
+    peq_slice(a.peq, blockIdx.y == 1, a.codemap, a.sigma_rows);
+    return;
+  }
+  const uint32_t yj = blockIdx.y - a.npeq;
+  if (yj < a.njobs) {
+    const XoffJob& J = a.job[yj];
     const uint32_t zero_code = *a.sigma_rows - 1;
     const uint64_t front = (uint64_t)kPadRowblocks * a.B + J.pad_front;
     const uint64_t total = (J.R + (uint64_t)kPadRowblocks + kPadBackRowblocks) * a.B;
@@ -161,13 +173,13 @@ __global__ void k_xoff(const __grid_constant__ XoffArgs a) {
 // 32q + k + 1; ballots of the code's bits give bit planes, and the mask of symbol r is the AND over the planes of
 // the plane (bit b of r set) or its complement (not set), restricted to the columns that exist. Lane r writes
 // row r (32 rows per pass up to sigma). Row sigma, the zero row, matches no column and comes out zero, and so do
-// the words past the end of Y, so nothing needs clearing first. blockIdx.y = 1: the masks over reversed Y.
-__global__ void k_peq(const uint8_t* __restrict__ y, uint64_t n, uint64_t wpad, const uint16_t* __restrict__ codemap,
-                      const uint32_t* __restrict__ sigma_rows, uint32_t* __restrict__ peq_f,
-                      uint32_t* __restrict__ peq_r) {
+// the words past the end of Y, so nothing needs clearing first. rev: the masks over reversed Y.
+__device__ void peq_slice(const PeqJob& P, bool rev, const uint16_t* __restrict__ codemap,
+                          const uint32_t* __restrict__ sigma_rows) {
+  const uint8_t* __restrict__ y = P.y;
+  const uint64_t n = P.n, wpad = P.wpad;
   const uint32_t lane = threadIdx.x & 31;
-  const bool rev = blockIdx.y == 1;
-  uint32_t* peq = rev ? peq_r : peq_f;
+  uint32_t* peq = rev ? P.peq_r : P.peq_f;
   const uint32_t sigma = *sigma_rows - 1;
   const uint32_t nb = 32 - __clz(sigma);  // bits of the codes 0..sigma
   const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -212,10 +224,17 @@ cudaError_t launch_alphabet(const uint8_t* y, uint64_t n, uint32_t* presence8, u
 }
 
 cudaError_t launch_xoff(const XoffJob* jobs, int njobs, uint32_t B, const uint16_t* codemap,
-                        const uint32_t* sigma_rows, const ZeroSpan* zero, int nzero, cudaStream_t st) {
+                        const uint32_t* sigma_rows, const ZeroSpan* zero, int nzero, const PeqJob* peq,
+                        cudaStream_t st) {
   if (njobs < 0 || njobs > 2 || nzero < 0 || nzero > kMaxZeroSpans) return cudaErrorInvalidValue;
   XoffArgs a{};
   uint64_t most = 1;
+  unsigned gx = 1;
+  if (peq) {
+    a.peq = *peq;
+    a.npeq = peq->peq_r ? 2u : 1u;
+    gx = grid_for(peq->wpad * 32, 256);  // a warp per word
+  }
   for (int k = 0; k < njobs; ++k) {
     a.job[k] = jobs[k];
     const uint64_t total = (jobs[k].R + (uint64_t)kPadRowblocks + kPadBackRowblocks) * B;
@@ -230,14 +249,8 @@ cudaError_t launch_xoff(const XoffJob* jobs, int njobs, uint32_t B, const uint16
   a.B = B;
   a.codemap = codemap;
   a.sigma_rows = sigma_rows;
-  k_xoff<<<dim3(grid_for(most, 256), (unsigned)njobs + 1), 256, 0, st>>>(a);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_peq(const uint8_t* y, uint64_t n, uint64_t wpad, const uint16_t* codemap,
-                       const uint32_t* sigma_rows, uint32_t* peq_f, uint32_t* peq_r, cudaStream_t st) {
-  k_peq<<<dim3(grid_for(wpad * 32, 256), peq_r ? 2u : 1u), 256, 0, st>>>(y, n, wpad, codemap, sigma_rows, peq_f,
-                                                                        peq_r);
+  gx = std::max(gx, grid_for(most, 256));
+  k_xoff<<<dim3(gx, a.npeq + (unsigned)njobs + 1), 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -1,6 +1,6 @@
 // Small pairs in one launch: LCS-length (paper §I.C) and Print-LCS (§I.D) for n <= 992 columns and m <= 1024 rows.
 //
-// The general path costs nine launches (alphabet, masks, row offsets, the cooperative fill, four traceback
+// The general path costs eight launches (alphabet, masks with row offsets, the cooperative fill, five traceback
 // kernels), which is most of the time of a pair of a few thousand cells. Here one warp does everything, in shared
 // memory:
 //   * match masks of all 256 byte values over Y, peq[c][q] bit k = [y[32q + k] = c] (absent bytes give zero rows);
