@@ -158,7 +158,8 @@ LCS_API int lcs_probe_step_masks(int device, uint32_t source, uint32_t steps, do
  * buffers, so they repeat too) is captured once as a CUDA graph, on its second occurrence, and replayed with one
  * launch from then on, instead of eight launches. The graph reads the buffers' contents when it runs. The capture
  * costs one extra host step once per new set of arguments; LCS_NO_PAIR_GRAPH=1 in the environment at context
- * creation turns it off. Pairs of the one-launch small path (see lcs_traceback) are never captured. */
+ * creation turns it off. Pairs of the one-launch small path (see lcs_traceback) are never captured. With stage
+ * timing on (lcs_ctx_set_profiling), the graph records the stage events too, so replayed calls are profiled. */
 
 /* Host buffers x[0..m), y[0..n); writes c[m,n] to *out_len. Blocking. m = 0 or n = 0 gives 0. Errors:
  * LCS_ERR_INVALID (NULL with nonzero size, out_len NULL), LCS_ERR_NOMEM, LCS_ERR_CUDA, LCS_ERR_TIMEOUT. */

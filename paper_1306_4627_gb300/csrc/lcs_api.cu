@@ -466,13 +466,14 @@ int run_traceback(lcs_ctx* c, const uint8_t* d_x, uint64_t m, const uint8_t* d_y
 // same buffers give their own results.
 
 // The arguments of a call and everything its launches take from the context: the fill configuration, the wait limit,
-// the test hook and the address of every device buffer.
+// the test hook, whether stage profiling is on (a profiled call's graph records the stage events) and the address of
+// every device buffer.
 static std::vector<uint64_t> pair_key(const lcs_ctx* c, bool traceback, const uint8_t* d_x, uint64_t m,
                                       const uint8_t* d_y, uint64_t n, const void* d_out, uint64_t out_cap,
                                       const void* d_out_len) {
   std::vector<uint64_t> k = {traceback ? 1u : 0u, (uint64_t)d_x, m, (uint64_t)d_y, n, (uint64_t)d_out, out_cap,
                              (uint64_t)d_out_len, c->fill_B, c->fill_B_tb, c->fill_variant, c->fill_variant_tb,
-                             c->spin_limit, c->debug_drop, (uint64_t)c->max_coop};
+                             c->spin_limit, c->debug_drop, (uint64_t)c->max_coop, c->prof ? 1u : 0u};
   const DBuf* bufs[] = {&c->small, &c->xoff_f, &c->xoff_r, &c->xcode, &c->peq_f, &c->peq_r, &c->carry_f, &c->carry_r,
                         &c->fv_f, &c->fv_r, &c->T, &c->snap_f, &c->snap_r, &c->colsum, &c->ent, &c->ext, &c->nch,
                         &c->entcnt, &c->sel, &c->chars, &c->cmap, &c->wlink};
@@ -486,12 +487,21 @@ int run_pair(lcs_ctx* c, bool traceback, const uint8_t* d_x, uint64_t m, const u
     return traceback ? run_traceback(c, d_x, m, d_y, n, d_out, out_cap, d_out_len, s)
                      : run_length(c, d_x, m, d_y, n, d_out_len, s);
   };
-  if (c->pgraph_off || c->prof || m == 0 || n == 0 || (c->small_path && small_pair(m, n))) return direct(st);
+  if (c->pgraph_off || m == 0 || n == 0 || (c->small_path && small_pair(m, n))) return direct(st);
   // every buffer of the call first, so that a capture never allocates
   int rc = traceback ? ensure_tb(c, tb_geo(c, m, n), m, true) : ensure_len(c, len_geo(c, m, n));
   if (rc) return rc;
   std::vector<uint64_t> key = pair_key(c, traceback, d_x, m, d_y, n, d_out, out_cap, d_out_len);
-  if (c->pexec && key == c->pkey) return from_cuda(cudaGraphLaunch(c->pexec, st));
+  if (c->pexec && key == c->pkey) {
+    rc = from_cuda(cudaGraphLaunch(c->pexec, st));
+    if (!rc && c->prof) {  // with profiling on, the graph records the stage events; the call is the captured one
+      c->prof_valid = true;
+      c->prof_trace = c->pprof_trace;
+      c->prof_blocks = c->pprof_blocks;
+      c->prof_cells = c->pprof_cells;
+    }
+    return rc;
+  }
   if (key != c->pseen) {  // the first call with these arguments is launched directly
     c->pseen = std::move(key);
     return direct(st);
@@ -520,6 +530,9 @@ int run_pair(lcs_ctx* c, bool traceback, const uint8_t* d_x, uint64_t m, const u
   }
   c->pexec = exec;
   c->pkey = std::move(key);
+  c->pprof_trace = c->prof_trace;  // what the capture set for the stage profile of this call
+  c->pprof_blocks = c->prof_blocks;
+  c->pprof_cells = c->prof_cells;
   return from_cuda(cudaGraphLaunch(c->pexec, st));
 }
 

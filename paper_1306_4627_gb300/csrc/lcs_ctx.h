@@ -90,8 +90,17 @@ struct lcs_ctx {
   bool prof = false, prof_valid = false, prof_trace = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   uint64_t prof_blocks = 0, prof_cells = 0;
+  // the same for a call captured into a graph (see run_pair): what the last call replayed reports
+  bool pprof_trace = false;
+  uint64_t pprof_blocks = 0, pprof_cells = 0;
   void mark(int k, cudaStream_t st) {
-    if (prof) cudaEventRecord(ev[k], st);
+    if (!prof) return;
+    // inside a stream capture the record becomes a node of the graph, which records the event each time it runs
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+      cudaEventRecordWithFlags(ev[k], st, cudaEventRecordExternal);
+    else
+      cudaEventRecord(ev[k], st);
   }
 
   uint16_t* codemap() { return (uint16_t*)((char*)small.p + lcs::kOffCodemap); }

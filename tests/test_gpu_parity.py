@@ -296,3 +296,31 @@ def test_segment_geometries_agree(oracle):
             assert dense.traceback(x, y) == want, (m, n)
             assert sparse.traceback(x, y) == want, (m, n)
     sparse.close()
+
+
+def test_profiled_repeated_calls_replay_with_stage_times(oracle):
+    """With stage timing on, repeated calls replay a graph that records the stage events: every call's result equals
+    the oracle's, and every call's profile has its fill and traceback stages inside its total."""
+    import torch
+    from paper_1306_4627_gb300 import lcs
+    d = torch.device("cuda", 0)
+    m, n = 3000, 2500
+    dx = torch.empty(m, dtype=torch.uint8, device=d)
+    dy = torch.empty(n, dtype=torch.uint8, device=d)
+    out = torch.zeros(min(m, n), dtype=torch.uint8, device=d)
+    out_len = torch.zeros(1, dtype=torch.int64, device=d)
+    with lcs.Context(0) as ctx:
+        ctx.set_profiling(True)
+        for k in range(4):
+            x, y = gen.pair_uniform(m, n, 4, seed=8100 + k)
+            dx.copy_(torch.from_numpy(x))
+            dy.copy_(torch.from_numpy(y))
+            ctx.traceback_dev(dx, dy, out, out_len)
+            p = ctx.last_profile()
+            ctx.sync()
+            L = int(out_len.item())
+            assert bytes(out[:L].cpu().numpy()) == oracle.lcs_traceback(x, y)
+            assert p["fill_ms"] > 0 and p["trace_ms"] > 0 and p["prep_ms"] >= 0
+            assert p["fill_ms"] + p["trace_ms"] <= p["total_ms"] * 1.001
+            assert p["cells"] == m * n
+        ctx.set_profiling(False)
