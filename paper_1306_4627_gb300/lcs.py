@@ -261,7 +261,7 @@ class Context:
     def traceback(self, x, y, out_cap: int | None = None) -> bytes:
         x, y = _u8(x), _u8(y)
         cap = min(len(x), len(y)) if out_cap is None else out_cap
-        out = np.zeros(max(cap, 1), dtype=np.uint8)
+        out = np.empty(max(cap, 1), dtype=np.uint8)
         n_out = ctypes.c_uint64(0)
         rc = _lib.lcs_traceback(self._h, _p8(x), len(x), _p8(y), len(y), _p8(out), cap, ctypes.byref(n_out))
         _check(rc, "lcs_traceback")
