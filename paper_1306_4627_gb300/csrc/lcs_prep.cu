@@ -42,23 +42,30 @@ __device__ __forceinline__ void for_my_bytes(const uint8_t* y, uint64_t n, F&& f
 }
 
 // One block (small and medium n): presence, then the code of a present byte = its rank among present bytes; an
-// absent byte maps to the all-zero row (index sigma). The presence takes one pass for which 32-value blocks occur
-// and one pass per occurring block when there are at most two (text alphabets), else one pass with a register
-// per block.
+// absent byte maps to the all-zero row (index sigma). The first pass finds which 32-value blocks occur and the OR of
+// the bytes' low five bits, which is the presence itself when one block occurs (DNA, protein letters); otherwise one
+// more pass per occurring block when there are two (text alphabets), else one pass with a register per block.
 __global__ void __launch_bounds__(1024) k_alphabet(const uint8_t* __restrict__ y, uint64_t n,
                                                    uint16_t* __restrict__ codemap, uint32_t* __restrict__ sigma_rows) {
   __shared__ uint32_t bits[8];
-  __shared__ uint32_t blocks_s;
+  __shared__ uint32_t blocks_s, low_s;
   if (threadIdx.x < 8) bits[threadIdx.x] = 0;
-  if (threadIdx.x == 0) blocks_s = 0;
+  if (threadIdx.x == 0) blocks_s = low_s = 0;
   __syncthreads();
-  uint32_t blocks = 0;
-  for_my_bytes(y, n, [&](uint32_t v) { blocks |= 1u << (v >> 5); });
+  uint32_t blocks = 0, low = 0;
+  for_my_bytes(y, n, [&](uint32_t v) {
+    blocks |= 1u << (v >> 5);
+    low |= 1u << (v & 31);
+  });
   blocks = __reduce_or_sync(kFull, blocks);
+  low = __reduce_or_sync(kFull, low);
   if ((threadIdx.x & 31) == 0 && blocks) atomicOr(&blocks_s, blocks);
+  if ((threadIdx.x & 31) == 0 && low) atomicOr(&low_s, low);
   __syncthreads();
   const uint32_t all = blocks_s;
-  if (__popc(all) <= 2) {
+  if (__popc(all) == 1) {
+    if (threadIdx.x == 0) bits[__ffs(all) - 1] = low_s;
+  } else if (__popc(all) == 2) {
     for (uint32_t bl = all; bl; bl &= bl - 1) {
       const uint32_t hi = __ffs(bl) - 1;
       uint32_t acc = 0;

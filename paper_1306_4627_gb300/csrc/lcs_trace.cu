@@ -27,29 +27,56 @@ constexpr uint32_t kFull = 0xFFFFFFFFu;
 constexpr uint64_t kWarpWalkers = 32;  // corridors of up to this many columns get a warp per walker
 
 // ---- word prefix popcounts of V rows ------------------------------------------------------------------------
-// For a V row (bit j-1 of the row = 1 - (c[i,j] - c[i,j-1])), pre[q] = ones among the first 32*q bits.
-// One block per row; each thread scans a contiguous run of words.
-__device__ void block_prefix_popc(const uint32_t* __restrict__ v, uint64_t w, uint32_t* __restrict__ pre) {
-  __shared__ uint32_t part[1024];
-  const uint32_t nt = blockDim.x, tid = threadIdx.x;
+// For a V row (bit j-1 of the row = 1 - (c[i,j] - c[i,j-1])), pre[q] = ones among the first 32*q bits, q = 0..w.
+// One block (a multiple of 32 threads, at most 1024) does NR rows at once: each thread sums a contiguous run of words
+// of every row, the runs' totals are scanned by shuffles within each warp and then over the warps' totals, and each
+// thread writes the prefixes of its runs.
+template <int NR>
+__device__ void block_prefix_popc(const uint32_t* const (&v)[NR], uint64_t w, uint32_t* const (&pre)[NR]) {
+  __shared__ uint32_t wsum[NR][32];
+  const uint32_t nt = blockDim.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   const uint64_t per = (w + nt - 1) / nt;
   const uint64_t q0 = tid * per, q1 = (q0 + per < w) ? q0 + per : w;
-  uint32_t s = 0;
-  for (uint64_t q = q0; q < q1; ++q) s += __popc(v[q]);
-  part[tid] = s;
+  uint32_t s[NR], incl[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    s[r] = 0;
+    for (uint64_t q = q0; q < q1; ++q) s[r] += __popc(v[r][q]);
+    incl[r] = s[r];
+  }
+  for (uint32_t off = 1; off < 32; off <<= 1) {  // inclusive scan of the run totals within the warp
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const uint32_t o = __shfl_up_sync(kFull, incl[r], off);
+      if (lane >= off) incl[r] += o;
+    }
+  }
+  if (lane == 31) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) wsum[r][wid] = incl[r];
+  }
   __syncthreads();
-  for (uint32_t off = 1; off < nt; off <<= 1) {  // Hillis-Steele inclusive scan over thread totals
-    const uint32_t add = tid >= off ? part[tid - off] : 0u;
-    __syncthreads();
-    part[tid] += add;
-    __syncthreads();
+  if (wid == 0) {  // inclusive scan of the warps' totals
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      uint32_t t = lane < nw ? wsum[r][lane] : 0u;
+      for (uint32_t off = 1; off < 32; off <<= 1) {
+        const uint32_t o = __shfl_up_sync(kFull, t, off);
+        if (lane >= off) t += o;
+      }
+      if (lane < nw) wsum[r][lane] = t;
+    }
   }
-  uint32_t run = part[tid] - s;
-  for (uint64_t q = q0; q < q1; ++q) {
-    pre[q] = run;
-    run += __popc(v[q]);
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    uint32_t run = (wid ? wsum[r][wid - 1] : 0u) + incl[r] - s[r];
+    for (uint64_t q = q0; q < q1; ++q) {
+      pre[r][q] = run;
+      run += __popc(v[r][q]);
+    }
+    if (tid == nt - 1) pre[r][w] = wsum[r][nw - 1];
   }
-  if (tid == nt - 1) pre[w] = part[tid];
   __syncthreads();
 }
 
@@ -62,7 +89,9 @@ __device__ __forceinline__ uint32_t ones_prefix(const uint32_t* v, const uint32_
 
 // ---- meet-in-the-middle length: L = n - min_j (ones_f(j) + ones_r(n - j)) -----------------------------------
 __global__ void k_combine_pre(const uint32_t* vf, const uint32_t* vr, uint64_t w, uint32_t* colsum) {
-  block_prefix_popc(blockIdx.x == 0 ? vf : vr, w, colsum + blockIdx.x * (w + 1));
+  const uint32_t* const v[1] = {blockIdx.x == 0 ? vf : vr};
+  uint32_t* const pre[1] = {colsum + blockIdx.x * (w + 1)};
+  block_prefix_popc<1>(v, w, pre);
   if (blockIdx.x == 0 && threadIdx.x == 0) colsum[2 * (w + 1)] = 0xFFFFFFFFu;  // running minimum
 }
 
@@ -135,8 +164,9 @@ __global__ void k_combine_fin(const uint32_t* colsum, uint64_t n, uint64_t w, un
 __global__ void k_corr_pre(TraceArgs a) {
   const uint64_t k = blockIdx.x + 1;
   const uint64_t wp1 = a.w + 1;
-  block_prefix_popc(a.snapF + (k - 1) * a.wpad, a.w, a.colsum + (2 * (k - 1)) * wp1);
-  block_prefix_popc(a.snapR + (a.S - k - 1) * a.wpad, a.w, a.colsum + (2 * (k - 1) + 1) * wp1);
+  const uint32_t* const v[2] = {a.snapF + (k - 1) * a.wpad, a.snapR + (a.S - k - 1) * a.wpad};
+  uint32_t* const pre[2] = {a.colsum + (2 * (k - 1)) * wp1, a.colsum + (2 * (k - 1) + 1) * wp1};
+  block_prefix_popc<2>(v, a.w, pre);
 }
 
 // Thread (q, boundary k): the columns j = 32q .. 32q + 31 (up to n) of the boundary's row. ones_f(j) comes from
