@@ -785,8 +785,8 @@ extern "C" int lcs_traceback(lcs_ctx* c, const uint8_t* x, uint64_t m, const uin
     rc = run_pair(c, true, (const uint8_t*)c->x.p, m, (const uint8_t*)c->y.p, n, (uint8_t*)c->out.p, cap,
                   c->out_len(), c->stream);
   // the string (at most min(m, n) bytes) comes back with the status and the length, behind one synchronisation. A
-  // copy into pageable memory would go through the CUDA runtime's own staging, synchronously: a pageable destination of
-  // up to kStageBytesMax bytes gets the string through the context's page-locked staging area instead (the input
+  // copy into pageable memory would go through the CUDA runtime's own staging, synchronously: a pageable destination
+  // of up to kStageBytesMax bytes gets the string through the context's page-locked staging area instead (the input
   // copies from it are done by then: stream order; it already holds m + n >= take bytes when they used it)
   const uint64_t take = std::min<uint64_t>(std::min(m, n), out_cap);
   const bool staged = take && take <= kStageBytesMax && !host_pinned(out) && ensure_hstage(c, take) == LCS_OK;

@@ -918,9 +918,9 @@ static int lcs_batch_impl(lcs_ctx* c, const uint8_t* xs, const uint64_t* x_off, 
   if (!rc)
     rc = run_batch(c, in_place ? vx : (const uint8_t*)c->x.p, in_place ? vy : (const uint8_t*)c->y.p, x_off, y_off,
                    count, (uint64_t*)c->bout.p, c->stream);
-  // the lengths come back through page-locked memory (a copy into pageable memory would go through the driver's own
-  // staging, synchronously): behind the staged strings, or at the start of the staging area when the strings did not
-  // use it (nothing of this call reads it then)
+  // the lengths come back through page-locked memory (a copy into pageable memory would go through the CUDA
+  // runtime's own staging, synchronously): behind the staged strings, or at the start of the staging area when the
+  // strings did not use it (nothing of this call reads it then)
   uint64_t* land = stage ? reinterpret_cast<uint64_t*>(c->hstage + ((nx + ny + 7) & ~(uint64_t)7)) : out_lens;
   if (stage && (uint8_t*)(land + count) > c->hstage + c->hstage_cap) land = out_lens;
   if (!rc && !stage && count * 8 <= kStageBytesMax && !host_pinned(out_lens) && ensure_hstage(c, count * 8) == LCS_OK)
